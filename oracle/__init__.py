@@ -1,0 +1,258 @@
+"""CPU oracle for the IWPP reconstruction and distance transform.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline / reference leg of ``bench.py`` may import this package.  It
+shares no code with the CUDA library (``paper_1209_3314_gb300``) and imports
+nothing from it; both sides only consume the same seeded inputs.
+
+What it provides (paper = Teodoro et al., arXiv:1209.3314):
+
+* ``fh(marker, mask, conn)`` -- fast hybrid reconstruction, Algorithm 2
+  (Section 2.1), sequential C (``iwpp_oracle.c``).
+* ``edt(binary, feature_nonzero)`` -- wavefront distance transform,
+  Algorithm 3 (Section 2.2), sequential C, FIFO order as published;
+  ``edt(..., policy=1|2)`` re-runs it with LIFO / random pop order.
+* ``edt_exact`` -- exact squared EDT (Meijster et al. 2000), sequential C.
+* ``recon_bruteforce`` -- the definition of reconstruction (Section 2.1):
+  elementary geodesic dilations, each clipped by the mask, to stability.
+* ``recon_threshold_decomposition`` -- the textbook binary decomposition:
+  for each level t, {out >= t} is the union of the connected components of
+  {mask >= t} that meet {marker and mask >= t}.  Independent of Algorithm 2.
+* ``edt_bruteforce`` -- the definition of the distance map (Section 2.2):
+  minimum squared distance to any feature pixel.
+* certificate checks of a result against the propagation rules.
+
+Every function takes and returns numpy arrays; the C part is built by
+``oracle/build.py`` (``gcc -O2 -shared``) on first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import build_oracle
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = build_oracle()
+        lib = ctypes.CDLL(path)
+        i32, i64p = ctypes.c_int, ctypes.POINTER(ctypes.c_int64)
+        vp = ctypes.c_void_p
+        lib.oracle_fh_i32.argtypes = [i32, i32, vp, vp, i32, i64p]
+        lib.oracle_fh_u8.argtypes = [i32, i32, vp, vp, i32, i64p]
+        lib.oracle_edt.argtypes = [i32, i32, vp, i32, vp, vp, i64p]
+        lib.oracle_edt_policy.argtypes = [i32, i32, vp, i32, vp, vp, i64p, i32,
+                                          ctypes.c_uint64]
+        lib.oracle_edt_exact.argtypes = [i32, i32, vp, i32, vp]
+        for f in ("oracle_fh_i32", "oracle_fh_u8", "oracle_edt",
+                  "oracle_edt_policy", "oracle_edt_exact"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def fh(marker: np.ndarray, mask: np.ndarray, conn: int = 8, stats: dict | None = None):
+    """Reconstruction of ``mask`` from ``marker`` by Algorithm 2 (FH).
+
+    uint8 or int32 2-D arrays of identical shape; returns a new array.
+    ``stats`` (optional dict) receives 'initial' and 'pushes' queue counts.
+    """
+    assert marker.shape == mask.shape and marker.ndim == 2
+    assert marker.dtype == mask.dtype
+    lib = _load()
+    h, w = mask.shape
+    I = np.ascontiguousarray(mask)
+    J = np.ascontiguousarray(marker).copy()
+    cnt = (ctypes.c_int64 * 2)()
+    if I.dtype == np.uint8:
+        rc = lib.oracle_fh_u8(h, w, _ptr(I), _ptr(J), conn, cnt)
+    elif I.dtype == np.int32:
+        rc = lib.oracle_fh_i32(h, w, _ptr(I), _ptr(J), conn, cnt)
+    else:
+        raise TypeError(f"unsupported dtype {I.dtype}")
+    if rc != 0:
+        raise RuntimeError("oracle_fh failed")
+    if stats is not None:
+        stats["initial"], stats["pushes"] = int(cnt[0]), int(cnt[1])
+    return J
+
+
+def edt(binary: np.ndarray, feature_nonzero: bool = False, policy: int = 0,
+        seed: int = 0, stats: dict | None = None):
+    """Algorithm 3: returns (sqdist int32, nearest int32 linear index).
+
+    Features are pixels equal to 0 (the paper's background) unless
+    ``feature_nonzero``.  No feature: sqdist INT32_MAX, nearest -1.
+    """
+    lib = _load()
+    b = np.ascontiguousarray(binary, dtype=np.uint8)
+    h, w = b.shape
+    nearest = np.empty((h, w), np.int32)
+    sq = np.empty((h, w), np.int32)
+    cnt = (ctypes.c_int64 * 2)()
+    rc = lib.oracle_edt_policy(h, w, _ptr(b), int(bool(feature_nonzero)),
+                               _ptr(nearest), _ptr(sq), cnt, int(policy), int(seed))
+    if rc != 0:
+        raise RuntimeError("oracle_edt failed")
+    if stats is not None:
+        stats["initial"], stats["pushes"] = int(cnt[0]), int(cnt[1])
+    return sq, nearest
+
+
+def edt_exact(binary: np.ndarray, feature_nonzero: bool = False) -> np.ndarray:
+    """Exact squared EDT (Meijster et al. 2000); INT32_MAX where no feature."""
+    lib = _load()
+    b = np.ascontiguousarray(binary, dtype=np.uint8)
+    h, w = b.shape
+    out = np.empty((h, w), np.int32)
+    if lib.oracle_edt_exact(h, w, _ptr(b), int(bool(feature_nonzero)), _ptr(out)) != 0:
+        raise RuntimeError("oracle_edt_exact failed")
+    return out
+
+
+# ---------------------------------------------------------------- definitions
+
+def _neighbour_max(J: np.ndarray, conn: int) -> np.ndarray:
+    """max over N_G(p) u {p}; pixels outside the image do not exist."""
+    if J.dtype == np.uint8:
+        low = 0
+    else:
+        low = np.iinfo(J.dtype).min
+    h, w = J.shape
+    P = np.full((h + 2, w + 2), low, dtype=J.dtype)
+    P[1:-1, 1:-1] = J
+    m = J.copy()
+    if conn == 8:
+        offs = [(-1, -1), (-1, 0), (-1, 1), (0, -1), (0, 1), (1, -1), (1, 0), (1, 1)]
+    else:
+        offs = [(-1, 0), (0, -1), (0, 1), (1, 0)]
+    for dy, dx in offs:
+        np.maximum(m, P[1 + dy:1 + dy + h, 1 + dx:1 + dx + w], out=m)
+    return m
+
+
+def recon_bruteforce(marker: np.ndarray, mask: np.ndarray, conn: int = 8,
+                     max_iter: int | None = None) -> np.ndarray:
+    """Section 2.1 definition: J <- (max over N_G(p) u {p} of J) and I(p),
+    starting from marker and mask, repeated until nothing changes."""
+    J = np.minimum(marker, mask)
+    it = 0
+    while True:
+        Jn = np.minimum(_neighbour_max(J, conn), mask)
+        it += 1
+        if np.array_equal(Jn, J):
+            return J
+        J = Jn
+        if max_iter is not None and it >= max_iter:
+            raise RuntimeError("brute force did not converge")
+
+
+def recon_threshold_decomposition(marker: np.ndarray, mask: np.ndarray,
+                                  conn: int = 8) -> np.ndarray:
+    """uint8 reconstruction by threshold decomposition and component labels.
+
+    out(p) = number of levels t in 1..255 at which p lies in a connected
+    component of {mask >= t} that contains a pixel with min(marker, mask) >= t.
+    """
+    from scipy import ndimage
+
+    assert mask.dtype == np.uint8
+    J0 = np.minimum(marker, mask)
+    structure = np.ones((3, 3), bool) if conn == 8 else ndimage.generate_binary_structure(2, 1)
+    out = np.zeros(mask.shape, np.int32)
+    lo = int(J0.min())
+    hi = int(J0.max())
+    out += lo  # every pixel's own component meets {J0 >= t} for t <= min(J0)
+    for t in range(max(lo + 1, 1), hi + 1):
+        lab, n = ndimage.label(mask >= t, structure=structure)
+        if n == 0:
+            break
+        hit = np.zeros(n + 1, bool)
+        hit[lab[J0 >= t]] = True
+        hit[0] = False
+        out += hit[lab]
+    return out.astype(np.uint8)
+
+
+def edt_bruteforce(binary: np.ndarray, feature_nonzero: bool = False) -> np.ndarray:
+    """Section 2.2 definition: squared distance to the nearest feature pixel."""
+    b = np.asarray(binary)
+    feat = (b != 0) if feature_nonzero else (b == 0)
+    h, w = b.shape
+    fy, fx = np.nonzero(feat)
+    if fy.size == 0:
+        return np.full((h, w), np.iinfo(np.int32).max, np.int32)
+    yy, xx = np.mgrid[0:h, 0:w]
+    d = (yy.reshape(-1, 1) - fy.reshape(1, -1)) ** 2 + (xx.reshape(-1, 1) - fx.reshape(1, -1)) ** 2
+    return d.min(axis=1).reshape(h, w).astype(np.int32)
+
+
+# ---------------------------------------------------------------- certificates
+
+def recon_unstable_pairs(out: np.ndarray, mask: np.ndarray, conn: int = 8) -> int:
+    """Number of (p, q) neighbour pairs where q could still be raised:
+    out(q) < min(out(p), mask(q)).  Zero exactly at a fixpoint of the
+    propagation rule of Algorithms 2 and 5."""
+    o = out.astype(np.int64)
+    m = mask.astype(np.int64)
+    return int((o < np.minimum(_neighbour_max(out, conn).astype(np.int64), m)).sum())
+
+
+def edt_certificate(binary: np.ndarray, sqdist: np.ndarray, nearest: np.ndarray,
+                    feature_nonzero: bool = False) -> dict:
+    """Checks a distance-transform result against the propagation rule.
+
+    Returns counts of violations of: nearest is a feature (or -1 with no
+    feature at all); sqdist equals |p - nearest(p)|^2; features have 0;
+    local optimality (no 8-neighbour's feature is strictly closer to p).
+    """
+    b = np.asarray(binary)
+    feat = (b != 0) if feature_nonzero else (b == 0)
+    h, w = b.shape
+    n = np.asarray(nearest).astype(np.int64)
+    sq = np.asarray(sqdist).astype(np.int64)
+    res = {}
+    valid = n >= 0
+    if not feat.any():
+        res["bad_nearest"] = int((n != -1).sum())
+        res["bad_sqdist"] = int((sq != np.iinfo(np.int32).max).sum())
+        res["feature_nonzero_dist"] = 0
+        res["not_locally_optimal"] = 0
+        return res
+    ny, nx = np.where(valid, n // w, 0), np.where(valid, n % w, 0)
+    in_range = valid & (n < h * w)
+    ff = feat.reshape(-1)[np.clip(n, 0, h * w - 1)].reshape(h, w)
+    res["bad_nearest"] = int((~in_range | ~ff).sum())
+    yy, xx = np.mgrid[0:h, 0:w]
+    d = (yy - ny) ** 2 + (xx - nx) ** 2
+    res["bad_sqdist"] = int((valid & (d != sq)).sum())
+    res["feature_nonzero_dist"] = int((feat & (sq != 0)).sum())
+    worse = 0
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dy == 0 and dx == 0:
+                continue
+            ys = slice(max(dy, 0), h + min(dy, 0))
+            xs = slice(max(dx, 0), w + min(dx, 0))
+            yd = slice(max(-dy, 0), h + min(-dy, 0))
+            xd = slice(max(-dx, 0), w + min(-dx, 0))
+            # candidate for pixel at (yd, xd) is the feature of its neighbour at (ys, xs)
+            cn = n[ys, xs]
+            cy, cx = cn // w, cn % w
+            py, px = yy[yd, xd], xx[yd, xd]
+            cd = (py - cy) ** 2 + (px - cx) ** 2
+            better = (cn >= 0) & ((sq[yd, xd] > cd) | (n[yd, xd] < 0))
+            worse += int(better.sum())
+    res["not_locally_optimal"] = worse
+    return res

@@ -1,0 +1,43 @@
+"""The seeded input generators: deterministic, right shapes and value
+ranges, coverage targets met."""
+import numpy as np
+
+from paper_1209_3314_gb300 import synth
+
+
+def test_blurred_noise_deterministic_and_full_range():
+    a = synth.blurred_noise_u8(200, 150, 4.0, seed=1)
+    b = synth.blurred_noise_u8(200, 150, 4.0, seed=1)
+    c = synth.blurred_noise_u8(200, 150, 4.0, seed=2)
+    np.testing.assert_array_equal(a, b)
+    assert not np.array_equal(a, c)
+    assert a.dtype == np.uint8 and a.min() == 0 and a.max() == 255
+
+
+def test_threaded_blur_matches_single_strip():
+    x = np.random.default_rng(0).random((1200, 1000))
+    from scipy.ndimage import correlate1d
+
+    k = synth._gauss_kernel(3.0)
+    ref = correlate1d(correlate1d(x, k, axis=1, mode="reflect"), k, axis=0, mode="reflect")
+    got = synth._blur_axis(synth._blur_axis(x, 3.0, 1), 3.0, 0)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_recon_inputs_marker_below_mask():
+    marker, mask = synth.recon_inputs(64, 80, 2.0, 40, seed=3)
+    assert (marker <= mask).all()
+    np.testing.assert_array_equal(marker, np.maximum(mask.astype(int) - 40, 0))
+
+
+def test_disks_coverage():
+    img, n = synth.disks_binary(512, 512, 4, 40, 0.3, seed=4)
+    assert set(np.unique(img)) <= {0, 1}
+    assert 0.3 <= img.mean() < 0.32 and n > 10
+
+
+def test_batched_workloads_shapes():
+    wls = synth.batched_workloads(n=6, seed=9, smin=32, smax=64)
+    assert [w.op for w in wls] == ["recon", "edt"] * 3
+    for w in wls:
+        assert 32 <= w.h <= 64 and 32 <= w.w <= 64
