@@ -1,0 +1,175 @@
+/*
+ * iwpp.h -- C ABI of libiwpp, a GB300 (sm_103a) implementation of the
+ * irregular wavefront propagation pattern (IWPP) of Teodoro, Pan, Kurc, Kong,
+ * Cooper and Saltz, "Efficient Irregular Wavefront Propagation Algorithms on
+ * Hybrid CPU-GPU Machines" (arXiv:1209.3314), for its two operations:
+ *
+ *   - grayscale morphological reconstruction by dilation (Section 2.1,
+ *     Algorithms 2 and 5);
+ *   - Euclidean distance transform by nearest-feature propagation
+ *     (Section 2.2, Algorithms 3 and 6).
+ *
+ * Conventions shared by every entry point
+ *   - Image buffers are DEVICE pointers owned by the caller, row-major, with
+ *     a pitch counted in elements (pitch >= w).  The library never frees or
+ *     retains them past the call's completion on the stream.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All work is enqueued on it.
+ *   - The context owns a device workspace (tile queues, flags, spill
+ *     buffers, counters) that it grows on demand; calls that share a context
+ *     must be ordered on one stream (two streams need two contexts).
+ *   - Synchronous entry points return after the work finished and the
+ *     device status word was read back; *_async entry points only enqueue
+ *     and report device-side failures at the next iwpp_sync().
+ *   - Return value: IWPP_OK or a negative IWPP_E* code; iwpp_last_error()
+ *     gives a one-line message.  No entry point aborts the process.
+ */
+#ifndef IWPP_H
+#define IWPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IWPP_OK 0
+#define IWPP_EINVAL (-1)    /* bad shape, dtype, pitch, connectivity or size  */
+#define IWPP_ENOMEM (-2)    /* workspace would exceed the HBM budget / cudaMalloc failed */
+#define IWPP_ECUDA (-3)     /* a CUDA runtime call failed                      */
+#define IWPP_ETIMEOUT (-4)  /* a device-side wait gave up (bounded spin)       */
+#define IWPP_EOVERFLOW (-5) /* tile queue overflowed more often than allowed   */
+
+typedef enum { IWPP_U8 = 0, IWPP_I32 = 1 } iwpp_dtype;
+
+/* Distance-transform polarity.  FEATURE_ZERO (default) is the paper's: the
+ * distance of every pixel to the nearest background (value 0) pixel
+ * (Section 2.2).  FEATURE_NONZERO measures the distance to the nearest
+ * non-zero pixel instead. */
+#define IWPP_EDT_FEATURE_ZERO 0
+#define IWPP_EDT_FEATURE_NONZERO 1
+
+typedef struct iwpp_ctx iwpp_ctx;
+
+/* A device image: data (device pointer), h rows, w columns, pitch in
+ * elements between row starts, dtype. */
+typedef struct {
+    void *data;
+    int32_t h, w;
+    int64_t pitch;
+    int32_t dtype; /* iwpp_dtype */
+} iwpp_image;
+
+/* Counters accumulated by a context since creation (or iwpp_stats_reset). */
+typedef struct {
+    uint64_t calls;            /* entry-point invocations                        */
+    uint64_t tiles_processed;  /* tile visits (first visits + re-visits)         */
+    uint64_t tiles_initial;    /* tiles in the initial queues                    */
+    uint64_t seeds;            /* wavefront seeds found by the tile seed scans   */
+    uint64_t pushes;           /* pixel-queue insertions during propagation      */
+    uint64_t spills;           /* insertions that went to the global spill queue */
+    uint64_t rescans;          /* tile rescans after the spill queue was full    */
+    uint64_t relaunches;       /* whole-image relaunches after tile-queue overflow */
+} iwpp_stats_t;
+
+/* Tunables; iwpp_get_options() fills the defaults.  tile = 0 lets the
+ * autotuner choose.  Values are validated by iwpp_set_options(). */
+typedef struct {
+    int32_t tile;            /* tile side in pixels: 0 (auto), 32, 64 or 128  */
+    int32_t blocks_per_sm;   /* persistent CTAs per SM, 0 = as many as fit    */
+    int32_t sweeps;          /* raster+anti-raster sweep pairs per tile visit  */
+    int32_t queue_factor;    /* tile-queue slots = queue_factor * tiles (>= 1) */
+    int32_t spill_cap;       /* global spill slots per CTA and buffer (>= 0)   */
+    int32_t max_relaunch;    /* device-side relaunches after queue overflow    */
+    int32_t timeout_ms;      /* bound on any device-side wait                  */
+    int32_t reserved[9];
+} iwpp_options;
+
+/* Creates a context on `device`.  hbm_budget_bytes bounds the workspace the
+ * context may hold (0 = unlimited).  *out receives the handle. */
+int iwpp_ctx_create(iwpp_ctx **out, int device, size_t hbm_budget_bytes);
+/* Waits for nothing; frees the workspace.  Passing NULL is a no-op. */
+int iwpp_ctx_destroy(iwpp_ctx *ctx);
+/* Message of the last failure on this context (never NULL). */
+const char *iwpp_last_error(const iwpp_ctx *ctx);
+
+int iwpp_get_options(const iwpp_ctx *ctx, iwpp_options *out);
+int iwpp_set_options(iwpp_ctx *ctx, const iwpp_options *opt);
+
+/*
+ * Morphological reconstruction by dilation of `mask` (I) from `marker` (J),
+ * Section 2.1 (definition: elementary geodesic dilations clipped by the
+ * mask, repeated to stability) computed by the tile-parallel wavefront of
+ * Algorithm 5.  conn = 4 or 8.  marker, mask and out share h, w and dtype
+ * (IWPP_U8 or IWPP_I32); pitches may differ.  out may alias marker (in
+ * place) but not mask.  A marker above the mask is first clipped to it.
+ * Result is exact (bit-identical to any correct sequential algorithm).
+ */
+int iwpp_recon(iwpp_ctx *ctx, const iwpp_image *marker, const iwpp_image *mask,
+               int conn, iwpp_image *out, void *stream);
+int iwpp_recon_async(iwpp_ctx *ctx, const iwpp_image *marker, const iwpp_image *mask,
+                     int conn, iwpp_image *out, void *stream);
+
+/*
+ * Distance transform by nearest-feature propagation, Section 2.2,
+ * Algorithms 3 and 6, 8-connected.  binary: IWPP_U8 image (0 / non-zero).
+ * Outputs (dense h*w int32, device): sqdist = squared Euclidean distance to
+ * the feature assigned to the pixel, nearest = that feature's linear index
+ * y*w + x.  With no feature in the image: sqdist = INT32_MAX, nearest = -1.
+ * Limits: max(h, w) <= 32768.  Like the paper's method, the assignment is
+ * approximate at rare pixels (Section 2.2, Figure 3): each result is a
+ * fixpoint of the propagation rule (no 8-neighbour's feature is strictly
+ * closer), and where several fixpoints exist the one reached may depend on
+ * the processing order.
+ */
+int iwpp_edt(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist,
+             int32_t *nearest, int flags, void *stream);
+int iwpp_edt_async(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist,
+                   int32_t *nearest, int flags, void *stream);
+
+/*
+ * Batched entry points: n independent images in ONE persistent launch
+ * (tiles of all images share one tile queue).  Arrays are host arrays of n
+ * descriptors / pointers; the images themselves are on the device.
+ */
+int iwpp_recon_batched(iwpp_ctx *ctx, int n, const iwpp_image *markers,
+                       const iwpp_image *masks, int conn, iwpp_image *outs,
+                       void *stream);
+int iwpp_edt_batched(iwpp_ctx *ctx, int n, const iwpp_image *bins,
+                     int32_t *const *sqdists, int32_t *const *nearests, int flags,
+                     void *stream);
+
+/* One job of a mixed batch: op 0 = reconstruction (a = marker, b = mask,
+ * out = result, conn), op 1 = distance transform (a = binary, sqdist,
+ * nearest, flags). */
+typedef struct {
+    int32_t op;
+    int32_t conn;
+    int32_t flags;
+    int32_t reserved;
+    iwpp_image a, b, out;
+    int32_t *sqdist, *nearest;
+} iwpp_job;
+
+#define IWPP_OP_RECON 0
+#define IWPP_OP_EDT 1
+
+/* Mixed reconstruction / distance-transform batch in one persistent launch. */
+int iwpp_run_jobs(iwpp_ctx *ctx, int n, const iwpp_job *jobs, void *stream);
+int iwpp_run_jobs_async(iwpp_ctx *ctx, int n, const iwpp_job *jobs, void *stream);
+
+/* Waits for `stream`, reads the device status of the async calls enqueued
+ * on it since the last sync, returns IWPP_OK or the first failure. */
+int iwpp_sync(iwpp_ctx *ctx, void *stream);
+
+int iwpp_stats(iwpp_ctx *ctx, iwpp_stats_t *out);
+int iwpp_stats_reset(iwpp_ctx *ctx);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int iwpp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IWPP_H */

@@ -1,0 +1,267 @@
+"""Thin ctypes binding over libiwpp (``include/iwpp.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch supplies device memory and streams; tensors are passed as
+raw device pointers with their row pitch.  There is no CPU fallback: if the
+library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB
+
+IWPP_OK = 0
+IWPP_EINVAL = -1
+IWPP_ENOMEM = -2
+IWPP_ECUDA = -3
+IWPP_ETIMEOUT = -4
+IWPP_EOVERFLOW = -5
+IWPP_U8 = 0
+IWPP_I32 = 1
+IWPP_EDT_FEATURE_ZERO = 0
+IWPP_EDT_FEATURE_NONZERO = 1
+IWPP_OP_RECON = 0
+IWPP_OP_EDT = 1
+
+# every function the header declares, with (restype, argtypes)
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int
+
+
+class Image(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("h", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("pitch", ctypes.c_int64), ("dtype", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "calls", "tiles_processed", "tiles_initial", "seeds", "pushes", "spills",
+        "rescans", "relaunches")]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("sweeps", ctypes.c_int32), ("queue_factor", ctypes.c_int32),
+                ("spill_cap", ctypes.c_int32), ("max_relaunch", ctypes.c_int32),
+                ("timeout_ms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("conn", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("a", Image), ("b", Image), ("out", Image),
+                ("sqdist", ctypes.c_void_p), ("nearest", ctypes.c_void_p)]
+
+
+SIGNATURES = {
+    "iwpp_version": (_i32, []),
+    "iwpp_ctx_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.c_size_t]),
+    "iwpp_ctx_destroy": (_i32, [_vp]),
+    "iwpp_last_error": (ctypes.c_char_p, [_vp]),
+    "iwpp_get_options": (_i32, [_vp, ctypes.POINTER(Options)]),
+    "iwpp_set_options": (_i32, [_vp, ctypes.POINTER(Options)]),
+    "iwpp_recon": (_i32, [_vp, ctypes.POINTER(Image), ctypes.POINTER(Image), _i32,
+                          ctypes.POINTER(Image), _vp]),
+    "iwpp_recon_async": (_i32, [_vp, ctypes.POINTER(Image), ctypes.POINTER(Image), _i32,
+                                ctypes.POINTER(Image), _vp]),
+    "iwpp_edt": (_i32, [_vp, ctypes.POINTER(Image), _vp, _vp, _i32, _vp]),
+    "iwpp_edt_async": (_i32, [_vp, ctypes.POINTER(Image), _vp, _vp, _i32, _vp]),
+    "iwpp_recon_batched": (_i32, [_vp, _i32, ctypes.POINTER(Image), ctypes.POINTER(Image), _i32,
+                                  ctypes.POINTER(Image), _vp]),
+    "iwpp_edt_batched": (_i32, [_vp, _i32, ctypes.POINTER(Image), ctypes.POINTER(_vp),
+                                ctypes.POINTER(_vp), _i32, _vp]),
+    "iwpp_run_jobs": (_i32, [_vp, _i32, ctypes.POINTER(Job), _vp]),
+    "iwpp_run_jobs_async": (_i32, [_vp, _i32, ctypes.POINTER(Job), _vp]),
+    "iwpp_sync": (_i32, [_vp, _vp]),
+    "iwpp_stats": (_i32, [_vp, ctypes.POINTER(Stats)]),
+    "iwpp_stats_reset": (_i32, [_vp]),
+}
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Loads libiwpp.so (built by ``paper_1209_3314_gb300.build``).  Raises if
+    it is missing: there is no fallback implementation."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB
+    if not os.path.exists(p):
+        raise ImportError(f"libiwpp not built ({p} missing); run paper_1209_3314_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class IWPPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"iwpp error {code}: {msg}")
+        self.code = code
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def image_of(t) -> Image:
+    """Describes a 2-D CUDA tensor (uint8 or int32, unit column stride)."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("expected a 2-D tensor with unit column stride")
+    if t.dtype == torch.uint8:
+        dt = IWPP_U8
+    elif t.dtype == torch.int32:
+        dt = IWPP_I32
+    else:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return Image(t.data_ptr(), t.shape[0], t.shape[1], max(t.stride(0), t.shape[1]), dt)
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """An iwpp context on one device: owns the library workspace."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        rc = self.lib.iwpp_ctx_create(ctypes.byref(h), device, hbm_budget)
+        if rc != IWPP_OK:
+            raise IWPPError(rc, "iwpp_ctx_create failed")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.iwpp_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != IWPP_OK:
+            raise IWPPError(rc, self.lib.iwpp_last_error(self.h).decode())
+
+    # ---- options / stats
+    def options(self) -> dict:
+        o = Options()
+        self._check(self.lib.iwpp_get_options(self.h, ctypes.byref(o)))
+        return {k: getattr(o, k) for k, _ in Options._fields_ if k != "reserved"}
+
+    def set_options(self, **kw):
+        o = Options()
+        self._check(self.lib.iwpp_get_options(self.h, ctypes.byref(o)))
+        for k, v in kw.items():
+            if k == "reserved" or not hasattr(o, k):
+                raise KeyError(k)
+            setattr(o, k, int(v))
+        self._check(self.lib.iwpp_set_options(self.h, ctypes.byref(o)))
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self.lib.iwpp_stats(self.h, ctypes.byref(s)))
+        return {k: int(getattr(s, k)) for k, _ in Stats._fields_}
+
+    def stats_reset(self):
+        self._check(self.lib.iwpp_stats_reset(self.h))
+
+    def sync(self, stream=None):
+        self._check(self.lib.iwpp_sync(self.h, _stream_ptr(stream)))
+
+    # ---- operations
+    def recon(self, marker, mask, conn: int = 8, out=None, stream=None, sync: bool = True):
+        """Reconstruction by dilation of ``mask`` from ``marker`` (CUDA
+        tensors, uint8 or int32).  Returns ``out`` (new tensor unless given;
+        ``out=marker`` reconstructs in place)."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty_like(mask)
+        m, k, o = image_of(marker), image_of(mask), image_of(out)
+        fn = self.lib.iwpp_recon if sync else self.lib.iwpp_recon_async
+        self._check(fn(self.h, ctypes.byref(m), ctypes.byref(k), conn, ctypes.byref(o),
+                       _stream_ptr(stream)))
+        return out
+
+    def edt(self, binary, feature_nonzero: bool = False, sqdist=None, nearest=None,
+            stream=None, sync: bool = True):
+        """Distance transform of a uint8 CUDA tensor.  Returns
+        (sqdist int32, nearest int32 linear index)."""
+        torch = _torch()
+        h, w = binary.shape
+        if sqdist is None:
+            sqdist = torch.empty((h, w), dtype=torch.int32, device=binary.device)
+        if nearest is None:
+            nearest = torch.empty((h, w), dtype=torch.int32, device=binary.device)
+        for t in (sqdist, nearest):
+            if t.dtype != torch.int32 or tuple(t.shape) != (h, w) or not t.is_contiguous() or not t.is_cuda:
+                raise ValueError("sqdist/nearest must be contiguous int32 CUDA tensors of the image shape")
+        b = image_of(binary)
+        fn = self.lib.iwpp_edt if sync else self.lib.iwpp_edt_async
+        flags = IWPP_EDT_FEATURE_NONZERO if feature_nonzero else IWPP_EDT_FEATURE_ZERO
+        self._check(fn(self.h, ctypes.byref(b), ctypes.c_void_p(sqdist.data_ptr()),
+                       ctypes.c_void_p(nearest.data_ptr()), flags, _stream_ptr(stream)))
+        return sqdist, nearest
+
+    def recon_batched(self, markers, masks, conn: int = 8, outs=None, stream=None):
+        torch = _torch()
+        n = len(markers)
+        if outs is None:
+            outs = [torch.empty_like(m) for m in masks]
+        M = (Image * n)(*[image_of(t) for t in markers])
+        K = (Image * n)(*[image_of(t) for t in masks])
+        O = (Image * n)(*[image_of(t) for t in outs])
+        self._check(self.lib.iwpp_recon_batched(self.h, n, M, K, conn, O, _stream_ptr(stream)))
+        return outs
+
+    def edt_batched(self, bins, feature_nonzero: bool = False, stream=None):
+        torch = _torch()
+        n = len(bins)
+        sq = [torch.empty(b.shape, dtype=torch.int32, device=b.device) for b in bins]
+        nn = [torch.empty(b.shape, dtype=torch.int32, device=b.device) for b in bins]
+        B = (Image * n)(*[image_of(t) for t in bins])
+        S = (ctypes.c_void_p * n)(*[t.data_ptr() for t in sq])
+        N = (ctypes.c_void_p * n)(*[t.data_ptr() for t in nn])
+        flags = IWPP_EDT_FEATURE_NONZERO if feature_nonzero else IWPP_EDT_FEATURE_ZERO
+        self._check(self.lib.iwpp_edt_batched(self.h, n, B, S, N, flags, _stream_ptr(stream)))
+        return list(zip(sq, nn))
+
+    def run_jobs(self, jobs, stream=None, sync: bool = True):
+        """Mixed batch in one launch.  ``jobs``: list of dicts, either
+        {'op': 'recon', 'marker', 'mask', 'out', 'conn'} or
+        {'op': 'edt', 'binary', 'sqdist', 'nearest', 'feature_nonzero'}."""
+        n = len(jobs)
+        arr = (Job * n)()
+        for i, j in enumerate(jobs):
+            if j["op"] == "recon":
+                arr[i].op = IWPP_OP_RECON
+                arr[i].conn = int(j.get("conn", 8))
+                arr[i].a = image_of(j["marker"])
+                arr[i].b = image_of(j["mask"])
+                arr[i].out = image_of(j["out"])
+            else:
+                arr[i].op = IWPP_OP_EDT
+                arr[i].flags = IWPP_EDT_FEATURE_NONZERO if j.get("feature_nonzero") else 0
+                arr[i].a = image_of(j["binary"])
+                arr[i].sqdist = j["sqdist"].data_ptr()
+                arr[i].nearest = j["nearest"].data_ptr()
+        fn = self.lib.iwpp_run_jobs if sync else self.lib.iwpp_run_jobs_async
+        self._check(fn(self.h, n, arr, _stream_ptr(stream)))

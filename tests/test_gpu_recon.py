@@ -1,0 +1,193 @@
+"""Reconstruction on the GPU through the C ABI, bit-exact against the CPU
+oracle (Algorithm 2) on seeded inputs: tiny and ragged images, several
+tiles, both connectivities, uint8 and int32, in place and pitched, forced
+queue overflow / spill / rescan paths, and the full 16384^2 workload."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1209_3314_gb300 import IWPPError, synth
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def run(ctx, marker, mask, conn=8, **opts):
+    if opts:
+        old = ctx.options()
+        ctx.set_options(**opts)
+    try:
+        out = ctx.recon(gpu(marker), gpu(mask), conn=conn)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+    finally:
+        if opts:
+            ctx.set_options(**old)
+
+
+def test_golden_small_cases(cuda_ctx):
+    with open(os.path.join(GOLDEN, "recon_small.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        I = np.array(c["mask"], np.uint8)
+        J = np.array(c["marker"], np.uint8)
+        np.testing.assert_array_equal(run(cuda_ctx, J, I, 8), np.array(c["out8"], np.uint8))
+        np.testing.assert_array_equal(run(cuda_ctx, J, I, 4), np.array(c["out4"], np.uint8))
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("dtype", [np.uint8, np.int32])
+@pytest.mark.parametrize("tile", [32, 64])
+def test_random_ragged(cuda_ctx, conn, dtype, tile):
+    rng = np.random.default_rng(1000 + conn + tile + (dtype == np.int32))
+    for _ in range(12):
+        h, w = (int(v) for v in rng.integers(1, 200, 2))
+        if dtype == np.uint8:
+            I = rng.integers(0, 256, (h, w)).astype(np.uint8)
+            J = rng.integers(0, 256, (h, w)).astype(np.uint8)  # exceeds the mask in places
+        else:
+            I = rng.integers(-2**31, 2**31 - 1, (h, w), dtype=np.int64).astype(np.int32)
+            J = (I.astype(np.int64) - rng.integers(0, 2**31, (h, w))).clip(-2**31, 2**31 - 1).astype(np.int32)
+        np.testing.assert_array_equal(run(cuda_ctx, J, I, conn, tile=tile), oracle.fh(J, I, conn))
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("tile", [32, 64])
+def test_config_512(cuda_ctx, conn, tile):
+    wl = synth.config_workload("recon512")
+    np.testing.assert_array_equal(run(cuda_ctx, wl.marker, wl.mask, conn, tile=tile),
+                                  oracle.fh(wl.marker, wl.mask, conn))
+
+
+def test_config_4096_and_int32_variant(cuda_ctx):
+    wl = synth.config_workload("recon4096")
+    ref = oracle.fh(wl.marker, wl.mask, 8)
+    np.testing.assert_array_equal(run(cuda_ctx, wl.marker, wl.mask, 8), ref)
+    # int32: the same values widened and shifted into the negative range
+    J = wl.marker.astype(np.int32) * 1000 - 70000
+    I = wl.mask.astype(np.int32) * 1000 - 70000
+    np.testing.assert_array_equal(run(cuda_ctx, J, I, 8), ref.astype(np.int32) * 1000 - 70000)
+
+
+@pytest.mark.parametrize("sweeps", [0, 1, 3])
+def test_sweep_count_does_not_change_result(cuda_ctx, sweeps):
+    marker, mask = synth.recon_inputs(700, 513, 6.0, 50, seed=21)
+    np.testing.assert_array_equal(run(cuda_ctx, marker, mask, 8, sweeps=sweeps), oracle.fh(marker, mask, 8))
+
+
+def test_in_place_and_pitched(cuda_ctx):
+    marker, mask = synth.recon_inputs(333, 301, 4.0, 40, seed=8)
+    ref = oracle.fh(marker, mask, 8)
+    m = gpu(marker)
+    cuda_ctx.recon(m, gpu(mask), conn=8, out=m)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(m.cpu().numpy(), ref)
+    # pitched views: rows of a wider buffer
+    big_m = torch.zeros((333, 400), dtype=torch.uint8, device=DEV)
+    big_k = torch.zeros((333, 352), dtype=torch.uint8, device=DEV)
+    big_o = torch.full((333, 384), 7, dtype=torch.uint8, device=DEV)
+    big_m[:, :301] = gpu(marker)
+    big_k[:, 17:318] = gpu(mask)
+    out = cuda_ctx.recon(big_m[:, :301], big_k[:, 17:318], conn=8, out=big_o[:, 50:351])
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), ref)
+    assert (big_o[:, :50] == 7).all() and (big_o[:, 351:] == 7).all()
+
+
+def test_forced_tile_queue_overflow_relaunch(cuda_ctx):
+    """Section 3.2 / 5.2.4: a queue too small to hold the work drops items;
+    relaunching from the partial result gives the identical output."""
+    marker, mask = synth.recon_inputs(1024, 1024, 8.0, 60, seed=5)
+    ref = oracle.fh(marker, mask, 8)
+    cuda_ctx.stats_reset()
+    out = run(cuda_ctx, marker, mask, 8, tile=32, queue_factor=1, max_relaunch=40)
+    np.testing.assert_array_equal(out, ref)
+    assert cuda_ctx.stats()["relaunches"] > 0
+
+
+def test_overflow_limit_reports_error(cuda_ctx):
+    marker, mask = synth.recon_inputs(1024, 1024, 8.0, 60, seed=5)
+    old = cuda_ctx.options()
+    cuda_ctx.set_options(tile=32, queue_factor=1, max_relaunch=0)
+    try:
+        with pytest.raises(IWPPError) as e:
+            cuda_ctx.recon(gpu(marker), gpu(mask), conn=8)
+        assert e.value.code == -5
+    finally:
+        cuda_ctx.set_options(**old)
+    # the context stays usable
+    np.testing.assert_array_equal(run(cuda_ctx, marker, mask, 8), oracle.fh(marker, mask, 8))
+
+
+def test_spill_and_rescan_paths(cuda_ctx):
+    rng = np.random.default_rng(44)
+    mask = rng.integers(0, 256, (256, 320)).astype(np.uint8)
+    marker = np.maximum(mask.astype(np.int16) - 50, 0).astype(np.uint8)
+    ref = oracle.fh(marker, mask, 8)
+    for spill in (0, 64, 4096):
+        cuda_ctx.stats_reset()
+        np.testing.assert_array_equal(run(cuda_ctx, marker, mask, 8, tile=32, sweeps=0, spill_cap=spill), ref)
+        st = cuda_ctx.stats()
+        if spill == 0:
+            assert st["rescans"] > 0
+        if spill == 64:
+            assert st["spills"] > 0
+
+
+def test_degenerate_shapes_and_values(cuda_ctx):
+    rng = np.random.default_rng(2)
+    for h, w in ((1, 1), (1, 97), (97, 1), (2, 2), (65, 1), (1, 65)):
+        I = rng.integers(0, 256, (h, w)).astype(np.uint8)
+        J = rng.integers(0, 256, (h, w)).astype(np.uint8)
+        for conn in (4, 8):
+            np.testing.assert_array_equal(run(cuda_ctx, J, I, conn), oracle.fh(J, I, conn))
+    I = rng.integers(0, 256, (150, 170)).astype(np.uint8)
+    np.testing.assert_array_equal(run(cuda_ctx, I, I, 8), I)
+    np.testing.assert_array_equal(run(cuda_ctx, np.zeros_like(I), I, 8), np.zeros_like(I))
+    c = np.full((150, 170), 200, np.uint8)
+    j = rng.integers(0, 150, c.shape).astype(np.uint8)
+    np.testing.assert_array_equal(run(cuda_ctx, j, c, 8), np.full(c.shape, j.max(), np.uint8))
+
+
+def test_invalid_arguments_raise(cuda_ctx):
+    a = torch.zeros((8, 8), dtype=torch.uint8, device=DEV)
+    b = torch.zeros((8, 9), dtype=torch.uint8, device=DEV)
+    with pytest.raises(IWPPError):
+        cuda_ctx.recon(a, a.clone(), conn=6)
+    with pytest.raises(IWPPError):
+        cuda_ctx.recon(a, b)
+    m = torch.zeros((8, 8), dtype=torch.uint8, device=DEV)
+    with pytest.raises(IWPPError):
+        cuda_ctx.recon(a, m, out=m)
+    with pytest.raises(IWPPError):
+        cuda_ctx.recon(a, torch.zeros((8, 8), dtype=torch.int32, device=DEV))
+
+
+def test_async_calls_then_sync(cuda_ctx):
+    marker, mask = synth.recon_inputs(512, 600, 4.0, 40, seed=12)
+    ref = oracle.fh(marker, mask, 8)
+    outs = [cuda_ctx.recon(gpu(marker), gpu(mask), conn=8, sync=False) for _ in range(3)]
+    cuda_ctx.sync()
+    for o in outs:
+        np.testing.assert_array_equal(o.cpu().numpy(), ref)
+
+
+@pytest.mark.slow
+def test_full_16k(cuda_ctx):
+    """The 16384^2 workload in the configuration the benchmark times,
+    compared pixel for pixel with the oracle (and its int32 variant)."""
+    wl = synth.config_workload("recon16k")
+    ref = oracle.fh(wl.marker, wl.mask, 8)
+    np.testing.assert_array_equal(run(cuda_ctx, wl.marker, wl.mask, 8), ref)
+    J = wl.marker.astype(np.int32) - 128
+    I = wl.mask.astype(np.int32) - 128
+    np.testing.assert_array_equal(run(cuda_ctx, J, I, 8), ref.astype(np.int32) - 128)
