@@ -71,19 +71,31 @@ typedef struct {
     uint64_t spills;           /* insertions that went to the global spill queue */
     uint64_t rescans;          /* tile rescans after the spill queue was full    */
     uint64_t relaunches;       /* whole-image relaunches after tile-queue overflow */
+    uint64_t rounds;           /* propagation rounds summed over tile visits     */
+    uint64_t wait_ns;          /* time persistent CTAs spent waiting for a tile, summed */
+    uint64_t visit_ns;         /* time persistent CTAs spent visiting tiles, summed     */
+    uint64_t kernel_launches;  /* kernels this library launched                  */
+    uint64_t kernel_ns;        /* device time from the first to the last persistent
+                                  launch of each call, summed (only while the
+                                  `timing` option is set; resolved at iwpp_sync) */
 } iwpp_stats_t;
 
 /* Tunables; iwpp_get_options() fills the defaults.  tile = 0 lets the
  * autotuner choose.  Values are validated by iwpp_set_options(). */
 typedef struct {
-    int32_t tile;            /* tile side in pixels: 0 (auto), 32, 64 or 128  */
+    int32_t tile;            /* tile side in pixels: 0 (auto) or 64           */
     int32_t blocks_per_sm;   /* persistent CTAs per SM, 0 = as many as fit    */
-    int32_t sweeps;          /* raster+anti-raster sweep pairs per tile visit  */
+    int32_t sweeps;          /* raster+anti-raster sweep sets per bulk visit   */
     int32_t queue_factor;    /* tile-queue slots = queue_factor * tiles (>= 1) */
     int32_t spill_cap;       /* global spill slots per CTA and buffer (>= 0)   */
     int32_t max_relaunch;    /* device-side relaunches after queue overflow    */
     int32_t timeout_ms;      /* bound on any device-side wait                  */
-    int32_t reserved[9];
+    int32_t timing;          /* 1: bracket the persistent launches with CUDA
+                                events and add their duration to kernel_ns    */
+    int32_t revisit_sweep_min; /* reconstruction: a later visit of a tile runs
+                                the sweeps when more halo pixels than this can
+                                propagate inward, else only the queue       */
+    int32_t reserved[7];
 } iwpp_options;
 
 /* Creates a context on `device`.  hbm_budget_bytes bounds the workspace the

@@ -38,14 +38,15 @@ class Image(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "calls", "tiles_processed", "tiles_initial", "seeds", "pushes", "spills",
-        "rescans", "relaunches")]
+        "rescans", "relaunches", "rounds", "wait_ns", "visit_ns", "kernel_launches", "kernel_ns")]
 
 
 class Options(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("sweeps", ctypes.c_int32), ("queue_factor", ctypes.c_int32),
                 ("spill_cap", ctypes.c_int32), ("max_relaunch", ctypes.c_int32),
-                ("timeout_ms", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("timeout_ms", ctypes.c_int32), ("timing", ctypes.c_int32),
+                ("revisit_sweep_min", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class Job(ctypes.Structure):

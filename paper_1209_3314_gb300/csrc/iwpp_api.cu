@@ -25,7 +25,10 @@ struct iwpp_ctx {
     Control *h_ctl = nullptr;  // pinned host copy
     uint64_t calls = 0;
     uint64_t tiles_initial = 0;
-    int occupancy[2] = {0, 0};  // blocks per SM for tile 32 / 64
+    uint64_t launches = 0;
+    uint64_t kernel_ns = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending_events, free_events;
+    int occupancy[FAM_COUNT] = {0, 0, 0, 0};  // blocks per SM per kernel family
 };
 
 namespace {
@@ -69,13 +72,69 @@ bool overlaps(const iwpp_image *a, const iwpp_image *b) {
     return a0 < b1 && b0 < a1;
 }
 
-int pick_tile(const iwpp_ctx *ctx, const std::vector<JobDesc> &jobs) {
-    if (ctx->opt.tile) return ctx->opt.tile;
-    // autotuned rule: small images need more tiles than SMs, large ones
-    // amortise the halo better with the bigger tile
-    int64_t px = 0;
-    for (const JobDesc &j : jobs) px += (int64_t)j.h * j.w;
-    return px <= (int64_t)1536 * 1536 ? 32 : 64;
+// One persistent-kernel family per launch: a single-operation launch uses
+// the specialised kernel with the smallest shared-memory footprint.
+int pick_family(const std::vector<JobDesc> &jobs) {
+    bool r8 = false, r32 = false, e = false;
+    for (const JobDesc &j : jobs) {
+        if (j.op == OP_EDT) e = true;
+        else if (j.dtype == DT_U8) r8 = true;
+        else r32 = true;
+    }
+    if (e && !r8 && !r32) return FAM_EDT;
+    if (r8 && !r32 && !e) return FAM_RECON_U8;
+    if (r32 && !r8 && !e) return FAM_RECON_I32;
+    return FAM_MIXED;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// TMA map of a 2-D image with the tile box (tile + halo, first column
+// 16-byte aligned).  False when the image does not meet TMA's alignment
+// rules (16-byte aligned base, row pitch a multiple of 16 bytes); the
+// kernel then stages with plain loads.
+bool make_map(CUtensorMap *m, const void *base, int dtype, int h, int w, int64_t pitch_elems) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const size_t es = dtype == DT_U8 ? 1 : 4;
+    const uint64_t pitch_bytes = (uint64_t)pitch_elems * es;
+    if (((uintptr_t)base & 15) || (pitch_bytes & 15) || pitch_bytes >= (1ull << 40)) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
+    cuuint64_t strides[1] = {pitch_bytes};
+    cuuint32_t box[2] = {dtype == DT_U8 ? 96u : 72u, (cuuint32_t)(TILE + 2)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, dtype == DT_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_INT32, 2,
+                    const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+void make_maps(JobDesc &d) {
+    bool ok;
+    if (d.op == OP_RECON) {
+        ok = make_map(&d.tm[0], d.a, d.dtype, d.h, d.w, d.pa) && make_map(&d.tm[1], d.b, d.dtype, d.h, d.w, d.pb) &&
+             make_map(&d.tm[2], d.out, d.dtype, d.h, d.w, d.po);
+    } else {
+        ok = make_map(&d.tm[0], d.a, DT_U8, d.h, d.w, d.pa) && make_map(&d.tm[2], d.nearest, DT_I32, d.h, d.w, d.w);
+    }
+    d.use_tma = ok ? 1 : 0;
 }
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -133,17 +192,17 @@ int64_t layout_jobs(std::vector<JobDesc> &jobs, int tile) {
 // Runs (or enqueues) the whole launch sequence for `jobs`.
 int run(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, cudaStream_t st, bool sync) {
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    const int tile = pick_tile(ctx, jobs);
-    if (tile != 32 && tile != 64) return fail(ctx, IWPP_EINVAL, "tile %d unsupported", tile);
+    const int tile = TILE;
+    const int fam = pick_family(jobs);
     const int64_t ntiles = layout_jobs(jobs, tile);
+    for (JobDesc &j : jobs) make_maps(j);
     if (ntiles <= 0 || ntiles > (int64_t)1 << 28) return fail(ctx, IWPP_EINVAL, "tile count %lld out of range", (long long)ntiles);
     const int64_t cap64 = std::max<int64_t>(ntiles + 1, (int64_t)ctx->opt.queue_factor * ntiles);
     if (cap64 > ((int64_t)1 << 31) - 1) return fail(ctx, IWPP_EINVAL, "tile queue too large");
 
-    int &occ = ctx->occupancy[tile == 32 ? 0 : 1];
+    int &occ = ctx->occupancy[fam];
     if (occ == 0) {
-        int r = max_blocks_per_sm(tile, &occ);
-        if (r != 0) return cuda_fail(ctx, (cudaError_t)r, "occupancy query");
+        CK(family_occupancy(fam, &occ), "occupancy query");
         if (occ < 1) return fail(ctx, IWPP_ECUDA, "persistent kernel does not fit on an SM");
     }
     int bps = ctx->opt.blocks_per_sm > 0 ? std::min(ctx->opt.blocks_per_sm, occ) : occ;
@@ -158,7 +217,7 @@ int run(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, cudaStream_t st, bool sync) {
     const size_t o_state = take((size_t)ntiles * 4);
     const size_t o_visited = take((size_t)ntiles * 4);
     const size_t o_cnt = take(16);
-    const size_t o_spill = take((size_t)grid * 2 * std::max(1, ctx->opt.spill_cap) * 4);
+    const size_t o_spill = take((size_t)grid * 2 * std::max(1, ctx->opt.spill_cap) * sizeof(uint16_t));
     const size_t o_jobs = take(jobs.size() > 1 ? jobs.size() * sizeof(JobDesc) : 0);
     int rc = ensure_ws(ctx, off, st);
     if (rc) return rc;
@@ -179,22 +238,39 @@ int run(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, cudaStream_t st, bool sync) {
     ka.tq.cap = (unsigned)cap64;
     ka.tq.ntiles = (int)ntiles;
     ka.ctl = ctx->ctl;
-    ka.spill = (int *)(ws + o_spill);
+    ka.spill = (uint16_t *)(ws + o_spill);
     ka.spill_cap = std::max(0, ctx->opt.spill_cap);
     ka.sweeps = ctx->opt.sweeps;
+    ka.revisit_sweep_min = ctx->opt.revisit_sweep_min;
     ka.timeout_ns = (unsigned long long)ctx->opt.timeout_ms * 1000000ull;
 
     if (jobs.size() > 1)
         CK(cudaMemcpyAsync(ws + o_jobs, jobs.data(), jobs.size() * sizeof(JobDesc), cudaMemcpyHostToDevice, st),
            "job table upload");
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (ctx->opt.timing) {
+        if (ctx->free_events.empty()) {
+            CK(cudaEventCreate(&ev.first), "cudaEventCreate");
+            CK(cudaEventCreate(&ev.second), "cudaEventCreate");
+        } else {
+            ev = ctx->free_events.back();
+            ctx->free_events.pop_back();
+        }
+    }
     CK(launch_init(ka, 1, st), "launch fill_queue");
-    CK(launch_persistent(ka, tile, grid, st), "launch persistent");
+    if (ev.first) CK(cudaEventRecord(ev.first, st), "cudaEventRecord");
+    CK(launch_persistent(ka, fam, grid, st), "launch persistent");
     for (int k = 0; k < ctx->opt.max_relaunch; ++k) {
         CK(launch_decide(ka, 0, st), "launch decide");
         CK(launch_reset(ka, st), "launch reset");
-        CK(launch_persistent(ka, tile, grid, st), "launch persistent");
+        CK(launch_persistent(ka, fam, grid, st), "launch persistent");
+    }
+    if (ev.second) {
+        CK(cudaEventRecord(ev.second, st), "cudaEventRecord");
+        ctx->pending_events.push_back(ev);
     }
     CK(launch_decide(ka, 1, st), "launch decide");
+    ctx->launches += 3 + 3 * (uint64_t)ctx->opt.max_relaunch;
     ctx->calls += 1;
     ctx->tiles_initial += (uint64_t)ntiles;
     if (!sync) return IWPP_OK;
@@ -280,11 +356,12 @@ int iwpp_ctx_create(iwpp_ctx **out, int device, size_t hbm_budget_bytes) {
     ctx->budget = hbm_budget_bytes;
     ctx->opt.tile = 0;
     ctx->opt.blocks_per_sm = 0;
-    ctx->opt.sweeps = 1;
+    ctx->opt.sweeps = 2;
     ctx->opt.queue_factor = 32;
-    ctx->opt.spill_cap = 4096;
+    ctx->opt.spill_cap = 8192;
     ctx->opt.max_relaunch = 1;
     ctx->opt.timeout_ms = 10000;
+    ctx->opt.revisit_sweep_min = 0;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&ctx->ctl, sizeof(Control)) != cudaSuccess ||
@@ -305,6 +382,8 @@ int iwpp_ctx_destroy(iwpp_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->ctl) cudaFree(ctx->ctl);
+    for (auto &ev : ctx->pending_events) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
+    for (auto &ev : ctx->free_events) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
     delete ctx;
     return IWPP_OK;
@@ -320,10 +399,11 @@ int iwpp_get_options(const iwpp_ctx *ctx, iwpp_options *out) {
 
 int iwpp_set_options(iwpp_ctx *ctx, const iwpp_options *o) {
     if (!ctx || !o) return IWPP_EINVAL;
-    if (o->tile != 0 && o->tile != 32 && o->tile != 64) return fail(ctx, IWPP_EINVAL, "tile must be 0, 32 or 64");
+    if (o->tile != 0 && o->tile != TILE) return fail(ctx, IWPP_EINVAL, "tile must be 0 (auto) or %d", TILE);
     if (o->blocks_per_sm < 0 || o->sweeps < 0 || o->sweeps > 64 || o->queue_factor < 1 || o->queue_factor > 4096 ||
-        o->spill_cap < 0 || o->spill_cap > (1 << 24) || o->max_relaunch < 0 || o->max_relaunch > 64 ||
-        o->timeout_ms < 1 || o->timeout_ms > 600000)
+        o->spill_cap < 0 || o->spill_cap > (1 << 20) || o->max_relaunch < 0 || o->max_relaunch > 64 ||
+        o->timeout_ms < 1 || o->timeout_ms > 600000 || o->timing < 0 || o->timing > 1 ||
+        o->revisit_sweep_min < 0)
         return fail(ctx, IWPP_EINVAL, "option out of range");
     ctx->opt = *o;
     return IWPP_OK;
@@ -433,6 +513,14 @@ int iwpp_sync(iwpp_ctx *ctx, void *stream) {
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     CK(cudaMemcpyAsync(ctx->h_ctl, ctx->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st), "status readback");
     CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    for (auto &ev : ctx->pending_events) {
+        float ms = 0.f;
+        CK(cudaEventSynchronize(ev.second), "cudaEventSynchronize");
+        CK(cudaEventElapsedTime(&ms, ev.first, ev.second), "cudaEventElapsedTime");
+        ctx->kernel_ns += (uint64_t)((double)ms * 1e6);
+        ctx->free_events.push_back(ev);
+    }
+    ctx->pending_events.clear();
     const int errors = ctx->h_ctl->errors;
     if (errors) {
         CK(cudaMemsetAsync(&ctx->ctl->errors, 0, sizeof(int), st), "status reset");
@@ -458,6 +546,11 @@ int iwpp_stats(iwpp_ctx *ctx, iwpp_stats_t *out) {
     out->spills = c.spills;
     out->rescans = c.rescans;
     out->relaunches = c.relaunches;
+    out->rounds = c.rounds;
+    out->wait_ns = c.wait_ns;
+    out->visit_ns = c.visit_ns;
+    out->kernel_launches = ctx->launches;
+    out->kernel_ns = ctx->kernel_ns;
     return IWPP_OK;
 }
 
@@ -467,10 +560,13 @@ int iwpp_stats_reset(iwpp_ctx *ctx) {
     CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
     Control c;
     CK(cudaMemcpy(&c, ctx->ctl, sizeof c, cudaMemcpyDeviceToHost), "stats readback");
-    c.tiles_processed = c.seeds = c.pushes = c.spills = c.rescans = c.relaunches = 0;
+    c.tiles_processed = c.seeds = c.pushes = c.spills = c.rescans = c.relaunches = c.rounds = 0;
+    c.wait_ns = c.visit_ns = 0;
     CK(cudaMemcpy(ctx->ctl, &c, sizeof c, cudaMemcpyHostToDevice), "stats reset");
     ctx->calls = 0;
     ctx->tiles_initial = 0;
+    ctx->launches = 0;
+    ctx->kernel_ns = 0;
     return IWPP_OK;
 }
 

@@ -39,6 +39,9 @@ struct Control {
     unsigned long long spills;
     unsigned long long rescans;
     unsigned long long relaunches;
+    unsigned long long rounds;
+    unsigned long long wait_ns;   // summed time CTAs waited for a tile
+    unsigned long long visit_ns;  // summed time CTAs spent visiting tiles
 };
 
 // Tile queue: a linear array of `cap` slots filled once each.  Tickets

@@ -2,6 +2,7 @@
 // host side of the C ABI (iwpp_api.cu).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -12,12 +13,19 @@ namespace iwpp {
 enum : int { OP_RECON = 0, OP_EDT = 1 };
 enum : int { DT_U8 = 0, DT_I32 = 1 };
 
+// kernel families (one persistent-kernel instantiation each)
+enum : int { FAM_RECON_U8 = 0, FAM_RECON_I32 = 1, FAM_EDT = 2, FAM_MIXED = 3, FAM_COUNT = 4 };
+
+constexpr int TILE = 64;  // tile side in pixels
+
 // One image job inside a launch.  Tiles of job j have global ids
 // [tile_base, tile_base + tiles_x * tiles_y).
-struct JobDesc {
+struct alignas(64) JobDesc {
+    CUtensorMap tm[3];   // TMA maps: a, b, out/nearest (valid when use_tma)
     int op, dtype, conn, flags;
     int h, w, tiles_x, tiles_y;
     int tile_base;
+    int use_tma;
     int color_base[4];   // first initial-queue slot of each tile colour class
     const void *a;       // recon: marker      edt: binary
     const void *b;       // recon: mask
@@ -27,24 +35,26 @@ struct JobDesc {
     int64_t pa, pb, po;  // pitches in elements
 };
 
-struct KArgs {
-    const JobDesc *jobs;  // device array (njobs > 1) ...
-    JobDesc job0;         // ... or this copy when njobs == 1
+struct alignas(64) KArgs {
+    JobDesc job0;         // the job when njobs == 1
+    const JobDesc *jobs;  // device array when njobs > 1
     int njobs;
     int ntiles;
     TileQueue tq;
     Control *ctl;
-    int *spill;           // per CTA: 2 * spill_cap ints
+    uint16_t *spill;      // per CTA: 2 * spill_cap entries
     int spill_cap;
-    int sweeps;
+    int sweeps;           // raster + anti-raster sweep sets per bulk visit
+    int revisit_sweep_min;  // later visits sweep when more halo seeds than this
     unsigned long long timeout_ns;
 };
 
 // Launch helpers implemented in iwpp_kernels.cu.
-int smem_bytes(int tile);
-int max_blocks_per_sm(int tile, int *out);
+int family_threads(int fam);
+int family_smem(int fam);
+cudaError_t family_occupancy(int fam, int *blocks_per_sm);
 cudaError_t launch_init(const KArgs &ka, int first_attempt, cudaStream_t s);
-cudaError_t launch_persistent(const KArgs &ka, int tile, int grid, cudaStream_t s);
+cudaError_t launch_persistent(const KArgs &ka, int fam, int grid, cudaStream_t s);
 cudaError_t launch_decide(const KArgs &ka, int final_step, cudaStream_t s);
 cudaError_t launch_reset(const KArgs &ka, cudaStream_t s);
 

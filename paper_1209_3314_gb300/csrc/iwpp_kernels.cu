@@ -1,630 +1,1084 @@
-// iwpp_kernels.cu -- the persistent tile-wavefront kernel of libiwpp.
+// iwpp_kernels.cu -- the persistent tile-wavefront kernels of libiwpp.
 //
-// One kernel drains a queue of image tiles.  Visiting a tile means:
-//   1. stage the tile plus a 1-pixel halo in shared memory (the halo holds
-//      the current values of the neighbouring tiles, read only);
-//   2. seed sweeps (reconstruction): raster and anti-raster passes inside
-//      the tile, each split into a row pass and a column pass as in
-//      Algorithm 5 (N^{+,0}, N^{0,+}, N^{-,0}, N^{0,-});
-//   3. seed scan: every pixel of tile+halo that can still propagate into a
-//      tile pixel is queued (the full-neighbourhood test of Algorithm 5 for
-//      reconstruction; Algorithm 6's initial wavefront generalised to a
-//      partial result for the distance transform);
-//   4. wavefront propagation inside the tile in rounds over in/out queues
-//      (Algorithm 4): atomicMax updates for reconstruction (Algorithm 5),
-//      compare-and-swap retry updates for the distance transform
-//      (Algorithm 6); warp-aggregated enqueue into per-warp, per-block
-//      (shared) and per-CTA global spill queues (Section 3.2);
-//   5. store the tile, then test every tile-border pixel against the
-//      neighbouring tiles' current values; a neighbour that could still be
-//      updated is re-queued (the border-propagation step of Section 4, done
-//      on one device without a separate stage).
-// Tiles only ever write their own pixels, and values only move in one
-// direction (up for reconstruction, closer features for the distance
-// transform), so any interleaving of visits converges to the same fixpoint
-// as the sequential algorithms.
+// The image is cut into 64x64 tiles.  A persistent kernel drains a queue of
+// tiles (the tile-level form of the wavefront loop of Algorithms 1 and 4: a
+// tile is queued again whenever a neighbour can still propagate into it,
+// which is the border-propagation step of Section 4 done on one device).
+//
+// Visiting a tile:
+//   1. stage tile + 1-pixel halo in shared memory with TMA boxes (plain
+//      loads when the image pitch does not meet TMA alignment);
+//   2. reconstruction, first visit: raster and anti-raster sweeps, each
+//      split into a row and a column pass as in Algorithm 5 (N^{+,0},
+//      N^{0,+}, N^{-,0}, N^{0,-}), then one elementary geodesic dilation
+//      step whose changed pixels seed the queue (afterwards every pixel that
+//      can still propagate is queued: the role of Algorithm 5's
+//      full-neighbourhood seed test);
+//      distance transform, first visit: Algorithm 6's initialisation, with
+//      the features that can improve a neighbour as the wavefront;
+//      any later visit: only the halo can have changed (the interior was
+//      left stable), so the halo pixels that can propagate inward are the
+//      seeds;
+//   3. wavefront propagation inside the tile in rounds over in/out queues
+//      (Algorithm 4): a max-update for reconstruction (Algorithm 5), a
+//      min-update of the packed (squared distance, feature) word for the
+//      distance transform (Algorithm 6's compare-and-swap, done as one
+//      64-bit atomicMin); each thread keeps the up to 8 neighbours it
+//      queues as a bit mask (the per-thread queue of Section 3.2), a warp
+//      prefix sum over those counts reserves the warp's block-queue space
+//      with one shared atomic, and a block queue that is full spills to the
+//      CTA's global queue; items beyond both are dropped and the tile is
+//      rescanned (Section 3.2's restart from a partial result);
+//   4. store the tile, then test each border pixel against the neighbouring
+//      tiles' current values and queue every neighbour that could change.
+// Tiles only write their own pixels and values move one way (up for
+// reconstruction, towards closer features for the distance transform), so
+// every interleaving of visits reaches a fixpoint of the propagation rule.
 #include <climits>
 #include <cstdint>
 
 #include "iwpp_internal.h"
+#include "iwpp_tma.cuh"
 
 namespace iwpp {
 
-constexpr int NT = 256;      // threads per CTA
-constexpr int NW = NT / 32;  // warps per CTA
+constexpr int TS = TILE;       // 64
+constexpr int RR = TS + 2;     // staged rows / columns
+constexpr int QCAP_R = 2048;   // reconstruction block-queue entries per buffer
+constexpr int QCAP_E = 4096;   // distance-transform block-queue entries per buffer
 
-// shared header slots
+// u8 TMA box: columns x0-16 .. x0+79 (96), rows y0-1 .. y0+64 (66)
+constexpr int BU8_W = 96, BU8_BYTES = BU8_W * RR, BU8_PAD = 6400;
+// int32 TMA box: columns x0-4 .. x0+67 (72), rows y0-1 .. y0+64
+constexpr int BI32_W = 72, BI32_BYTES = BI32_W * RR * 4, BI32_PAD = 19072;
+// u8 working layout: row stride 76 bytes (19 words: an odd word stride keeps
+// one-row-per-thread walks free of bank conflicts); cell (r, c) at byte
+// r*76 + c + 3, so that word k of a row holds cells 4k-3 .. 4k and box word
+// k+3 maps onto working word k.
+constexpr int WU8_P = 76, WU8_PAD = 5120;
+// distance-transform working array: 64-bit words, row stride 67
+constexpr int WE_P = 67, WE_PAD = 35456;
+
+// shared header (ints)
 enum : int {
-    H_TILE = 0,
-    H_CNT0 = 1,   // round-queue counters (2)
-    H_RESCAN = 3,
-    H_SRC = 4,    // 3x3 neighbour tiles: 1 if visited (9)
-    H_FLAG = 13,  // 3x3 neighbour tiles: needs a visit (9)
-    H_PUSH = 22,
-    H_SPILL = 23,
-    H_RESC = 24,
-    H_SEEDS = 25,
-    H_WORDS = 64,
+    H_TILE = 0, H_CNT0 = 1, H_CNT1 = 2, H_RESCAN = 3,
+    H_SRC = 4,    // 3x3 neighbourhood: 0 unvisited tile, 1 visited, 2 outside the image
+    H_FLAG = 13,  // 3x3 neighbourhood: needs a visit
+    H_PUSH = 22, H_SPILL = 23, H_RESC = 24, H_SEEDS = 25, H_ROUNDS = 26,
+    H_OFF = 32,   // 9 neighbour offsets of the current layout
 };
+constexpr int HDR_BYTES = 512;  // header ints + mbarrier at byte 256
 
-template <int TS>
-struct Geo {
-    static constexpr int R = TS + 2;                       // staged rows/cols
-    static constexpr int P = (R % 2 == 0) ? R + 1 : R;     // odd pitch (words)
-    static constexpr int CELLS = R * P;
-    static constexpr int QCAP = TS * TS;                   // BQ entries per buffer
-    static constexpr int WORDS = H_WORDS + 2 * CELLS + 2 * QCAP + NW * 64;
-};
+// byte offsets of the layouts
+constexpr int RU8_JW = HDR_BYTES, RU8_IW = RU8_JW + WU8_PAD, RU8_U = RU8_IW + WU8_PAD;
+constexpr int RU8_BYTES = RU8_U + 3 * BU8_PAD;
+constexpr int RI32_J = HDR_BYTES, RI32_I = RI32_J + BI32_PAD, RI32_U = RI32_I + BI32_PAD;
+constexpr int RI32_BYTES = RI32_U + BI32_PAD;
+constexpr int E_W = HDR_BYTES, E_U = E_W + WE_PAD;
+constexpr int E_BYTES = E_U + BU8_PAD + BI32_PAD;
+static_assert(RU8_U % 128 == 0 && RI32_J % 128 == 0 && RI32_I % 128 == 0 && RI32_U % 128 == 0 &&
+                  E_U % 128 == 0 && (E_U + BU8_PAD) % 128 == 0,
+              "TMA destinations must be 128-byte aligned");
+static_assert(2 * QCAP_R * 2 <= 3 * BU8_PAD && 2 * QCAP_R * 2 <= BI32_PAD &&
+                  2 * QCAP_E * 2 <= BU8_PAD + BI32_PAD,
+              "queues must fit the staging union");
+static_assert(RR * WE_P * 8 <= WE_PAD, "EDT working array");
 
-struct Smem {
-    int *hdr, *A, *B, *Q0, *Q1, *WQ;
-};
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+constexpr int FAM_SMEM[FAM_COUNT] = {RU8_BYTES, RI32_BYTES, E_BYTES,
+                                     cmax(cmax(RU8_BYTES, RI32_BYTES), E_BYTES)};
+constexpr int FAM_NT[FAM_COUNT] = {64, 64, 128, 128};
 
-template <int TS>
-__device__ __forceinline__ Smem carve(int *base) {
-    using G = Geo<TS>;
-    Smem s;
-    s.hdr = base;
-    s.A = base + H_WORDS;
-    s.B = s.A + G::CELLS;
-    s.Q0 = s.B + G::CELLS;
-    s.Q1 = s.Q0 + G::QCAP;
-    s.WQ = s.Q1 + G::QCAP;
-    return s;
+// neighbourhood offsets (dy, dx); 8-connected: the first 4 are N+ (raster)
+__device__ __forceinline__ int nb_dy(int conn, int k) {
+    return conn == 8 ? (k < 3 ? -1 : (k < 5 ? 0 : 1)) : (k == 0 ? -1 : (k == 3 ? 1 : 0));
+}
+__device__ __forceinline__ int nb_dx(int conn, int k) {
+    return conn == 8 ? ((k == 0 || k == 3 || k == 5) ? -1 : ((k == 2 || k == 4 || k == 7) ? 1 : 0))
+                     : (k == 1 ? -1 : (k == 2 ? 1 : 0));
 }
 
-template <int CONN> struct Nb;
-template <> struct Nb<8> {
-    static __device__ __forceinline__ int dr(int k) { return k < 3 ? -1 : (k < 5 ? 0 : 1); }
-    static __device__ __forceinline__ int dc(int k) {
-        const int t[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
-        return t[k];
-    }
-};
-template <> struct Nb<4> {
-    static __device__ __forceinline__ int dr(int k) { return k == 0 ? -1 : (k == 3 ? 1 : 0); }
-    static __device__ __forceinline__ int dc(int k) { return k == 1 ? -1 : (k == 2 ? 1 : 0); }
-};
-
-template <typename T> struct Low;
-template <> struct Low<uint8_t> { static constexpr int v = -1; };
-template <> struct Low<int32_t> { static constexpr int v = INT_MIN; };
-
-__device__ __forceinline__ int ldcg_val(const uint8_t *p) { return (int)__ldcg(p); }
-__device__ __forceinline__ int ldcg_val(const int32_t *p) { return __ldcg(p); }
-__device__ __forceinline__ int ldg_val(const uint8_t *p) { return (int)__ldg(p); }
-__device__ __forceinline__ int ldg_val(const int32_t *p) { return __ldg(p); }
-
-__device__ __forceinline__ JobDesc job_of(const KArgs &ka, int t) {
-    if (ka.njobs == 1) return ka.job0;
+__device__ __forceinline__ const JobDesc *job_of(const KArgs &ka, int t) {
+    if (ka.njobs == 1) return &ka.job0;
     int lo = 0, hi = ka.njobs - 1;
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
+        const int mid = (lo + hi + 1) >> 1;
         if (__ldg(&ka.jobs[mid].tile_base) <= t) lo = mid; else hi = mid - 1;
     }
-    return ka.jobs[lo];
+    return ka.jobs + lo;
 }
 
-// Enumerates the 4*(TS+1) halo cells: top row, bottom row, left and right
-// columns (corners belong to the rows).
-template <int TS>
-__device__ __forceinline__ void halo_cell(int i, int &r, int &c) {
-    constexpr int R = TS + 2;
-    if (i < R) { r = 0; c = i; }
-    else if (i < 2 * R) { r = R - 1; c = i - R; }
-    else if (i < 2 * R + TS) { r = i - 2 * R + 1; c = 0; }
-    else { r = i - 2 * R - TS + 1; c = R - 1; }
+__device__ __forceinline__ int region(int v) { return v == 0 ? 0 : (v == RR - 1 ? 2 : 1); }
+
+// the k-th of the 4*(TS+1) halo cells: top row, bottom row, left, right
+__device__ __forceinline__ void halo_cell(int k, int &r, int &c) {
+    if (k < RR) { r = 0; c = k; }
+    else if (k < 2 * RR) { r = RR - 1; c = k - RR; }
+    else if (k < 2 * RR + TS) { r = k - 2 * RR + 1; c = 0; }
+    else { r = k - 2 * RR - TS + 1; c = RR - 1; }
 }
 
-__device__ __forceinline__ int region(int v, int last) { return v == 0 ? 0 : (v == last ? 2 : 1); }
-
-// Loads the 3x3 'visited' flags of the tile neighbourhood into hdr[H_SRC..].
-__device__ __forceinline__ void load_sources(const KArgs &ka, const JobDesc &jd, int tx, int ty, Smem s) {
+// 3x3 'visited' states of the tile neighbourhood -> hdr[H_SRC..]
+__device__ __forceinline__ void load_sources(const KArgs &ka, const JobDesc *jd, int tx, int ty, int *hdr) {
     const int tid = threadIdx.x;
     if (tid < 9) {
         const int ny = ty + tid / 3 - 1, nx = tx + tid % 3 - 1;
-        int v = 0;
-        if (ny >= 0 && ny < jd.tiles_y && nx >= 0 && nx < jd.tiles_x)
-            v = ld_acquire(ka.tq.visited + jd.tile_base + ny * jd.tiles_x + nx);
-        s.hdr[H_SRC + tid] = v;
+        int v = 2;
+        if (ny >= 0 && ny < jd->tiles_y && nx >= 0 && nx < jd->tiles_x)
+            v = ld_acquire(ka.tq.visited + jd->tile_base + ny * jd->tiles_x + nx) ? 1 : 0;
+        hdr[H_SRC + tid] = v;
     }
 }
 
-// Publishes the tile's stores, re-queues flagged neighbours, marks the tile
-// visited.  Thread 0 only; all stores of the CTA precede it (barrier).
-__device__ __forceinline__ void finish_tile(const KArgs &ka, const JobDesc &jd, int gt, int tx, int ty, Smem s) {
+__device__ __forceinline__ void begin_visit(int *hdr) {
+    const int tid = threadIdx.x;
+    if (tid < 9) hdr[H_FLAG + tid] = 0;
+    if (tid == 0) {
+        hdr[H_CNT0] = 0; hdr[H_CNT1] = 0; hdr[H_RESCAN] = 0;
+        hdr[H_PUSH] = 0; hdr[H_SPILL] = 0; hdr[H_RESC] = 0; hdr[H_SEEDS] = 0; hdr[H_ROUNDS] = 0;
+    }
+}
+
+// Publishes the tile's stores, queues flagged neighbours, marks the tile
+// visited and ends the visit.  Thread 0; all stores precede it (barrier).
+__device__ __forceinline__ void finish_tile(const KArgs &ka, const JobDesc *jd, int gt, int tx, int ty, int *hdr) {
     __threadfence();
-    if (!s.hdr[H_SRC + 4]) st_release(ka.tq.visited + gt, 1);
+    if (hdr[H_SRC + 4] != 1) st_release(ka.tq.visited + gt, 1);
     for (int k = 0; k < 9; ++k) {
-        if (k == 4 || !s.hdr[H_FLAG + k]) continue;
+        if (k == 4 || !hdr[H_FLAG + k]) continue;
         const int ny = ty + k / 3 - 1, nx = tx + k % 3 - 1;
-        tq_push(ka.tq, ka.ctl, jd.tile_base + ny * jd.tiles_x + nx);
+        tq_push(ka.tq, ka.ctl, jd->tile_base + ny * jd->tiles_x + nx);
     }
     tq_finish(ka.tq, ka.ctl, gt);
+}
+
+// neighbour offsets in a layout with row pitch P -> hdr[H_OFF..]; entry 8
+// is 0 (the pixel itself)
+template <int CONN, int P>
+__device__ __forceinline__ void make_offsets(int *hdr) {
+    if (threadIdx.x < 9) {
+        const int n = threadIdx.x;
+        hdr[H_OFF + n] = n < CONN ? nb_dy(CONN, n) * P + nb_dx(CONN, n) : 0;
+    }
+}
+
+// ------------------------------------------------------------ the queues
+
+// Round queue: virtual array [block queue in shared memory | CTA spill
+// queue in global memory]; entries past both are dropped (rescan flag).
+struct RQ {
+    uint16_t *s;
+    uint16_t *g;
+    int *count;
+    int *rescan;
+    int cap_s, cap_g;
+};
+
+__device__ __forceinline__ void rq_put(const RQ &q, int pos, int item) {
+    if (pos < q.cap_s) q.s[pos] = (uint16_t)item;
+    else if (pos - q.cap_s < q.cap_g) q.g[pos - q.cap_s] = (uint16_t)item;
+    else *q.rescan = 1;
+}
+
+__device__ __forceinline__ int rq_get(const uint16_t *s, const uint16_t *g, int cap_s, int i) {
+    return i < cap_s ? s[i] : __ldcg(g + (i - cap_s));
+}
+
+// Warp-aggregated enqueue: each lane holds up to 9 items as a neighbour bit
+// mask (its per-thread queue; bit 8 is the pixel itself); an inclusive warp
+// scan of the counts gives each lane its slots and the last lane reserves
+// the warp's total with one shared atomic.  Called by all 32 lanes.
+__device__ __forceinline__ unsigned warp_enqueue(unsigned mask, int p, const int *off, const RQ &q) {
+    const int lane = threadIdx.x & 31;
+    const int cnt = __popc(mask);
+    if (!__any_sync(0xffffffffu, cnt)) return 0;
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int base = 0;
+    if (lane == 31) base = atomicAdd(q.count, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    int pos = base + incl - cnt;
+    while (mask) {
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1;
+        rq_put(q, pos++, p + off[k]);
+    }
+    return (unsigned)total;
+}
+
+// Propagation rounds until the queue is empty (the loop of Algorithm 4).
+// proc(p): processes item p, returns the mask of neighbours it raised;
+// rescan(q): re-seeds the whole tile into q, returns the count.
+template <int NT, typename Proc, typename Rescan>
+__device__ void run_rounds(int *hdr, uint16_t *Q0, uint16_t *Q1, int qcap, uint16_t *spill, int spill_cap,
+                           const int *off, Proc proc, Rescan rescan) {
+    const int tid = threadIdx.x;
+    int cur = 0;
+    unsigned pushed = 0, spilled = 0, rescans = 0, rounds = 0;
+    while (true) {
+        __syncthreads();
+        const int n_raw = hdr[H_CNT0 + cur];
+        const int resc = hdr[H_RESCAN];
+        const int n_in = min(n_raw, qcap + spill_cap);
+        if (n_in == 0 && !resc) break;
+        __syncthreads();
+        if (tid == 0) {
+            hdr[H_CNT0 + (cur ^ 1)] = 0;
+            hdr[H_RESCAN] = 0;
+        }
+        spilled += n_in > qcap ? n_in - qcap : 0;
+        rescans += resc ? 1 : 0;
+        ++rounds;
+        __syncthreads();
+        const uint16_t *qs = cur ? Q1 : Q0;
+        const uint16_t *qg = spill + cur * spill_cap;
+        RQ out{cur ? Q0 : Q1, spill + (cur ^ 1) * spill_cap, hdr + H_CNT0 + (cur ^ 1), hdr + H_RESCAN, qcap,
+               spill_cap};
+        for (int base = 0; base < n_in; base += NT) {
+            const int i = base + tid;
+            const int p = i < n_in ? rq_get(qs, qg, qcap, i) : -1;
+            const unsigned m = p >= 0 ? proc(p) : 0u;
+            pushed += warp_enqueue(m, p, off, out);
+        }
+        if (resc) {
+            // the in-queue was truncated: what fitted was processed (progress),
+            // the next queue comes from a scan of the partial result
+            __syncthreads();
+            if (tid == 0) { hdr[H_CNT0 + (cur ^ 1)] = 0; hdr[H_RESCAN] = 0; }
+            __syncthreads();
+            pushed += rescan(out);
+        }
+        cur ^= 1;
+    }
+    if ((tid & 31) == 0) atomicAdd(hdr + H_PUSH, (int)pushed);
+    if (tid == 0) {
+        hdr[H_SPILL] = (int)spilled;
+        hdr[H_RESC] = (int)rescans;
+        hdr[H_ROUNDS] = (int)rounds;
+    }
+}
+
+// Plain (non-TMA) staging of a box with zero fill outside the image.
+template <typename T, int BW>
+__device__ void stage_plain(T *dst, const T *src, int64_t pitch, int h, int w, int bx, int by, int nt) {
+    for (int i = threadIdx.x; i < BW * RR; i += nt) {
+        const int r = i / BW, c = i - r * BW;
+        const int gy = by + r, gx = bx + c;
+        T v = 0;
+        if (gy >= 0 && gy < h && gx >= 0 && gx < w) v = __ldcg(src + (int64_t)gy * pitch + gx);
+        dst[i] = v;
+    }
+}
+
+// Waits for the visit's TMA boxes; on a timeout raises ST_TIMEOUT, gives the
+// copies a second bounded wait and tells the caller to abandon the kernel.
+__device__ __forceinline__ bool wait_boxes(uint64_t *bar, uint32_t &phase, unsigned long long deadline,
+                                           Control *ctl) {
+    const bool ok = mbar_wait(bar, phase, deadline);
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            atomicOr(&ctl->status, ST_TIMEOUT);
+            atomicOr(&ctl->sticky, ST_TIMEOUT);
+        }
+        mbar_wait(bar, phase, globaltimer_ns() + 1000000000ull);
+    }
+    phase ^= 1;
+    return __syncthreads_and(ok) != 0;
 }
 
 // =====================================================================
 // Reconstruction by dilation (Section 2.1; Algorithms 2, 4, 5)
 // =====================================================================
 
-template <int CONN, int TS>
-__device__ void recon_seed_scan(const int *J, const int *I, WarpQueue &wq, const RoundQueue &rq) {
-    using G = Geo<TS>;
-    constexpr int R = G::R, P = G::P;
-    for (int base = 0; base < R * R; base += NT) {
-        const int i = base + threadIdx.x;
-        bool seed = false;
-        int p = 0;
-        if (i < R * R) {
-            const int r = i / R, c = i - r * R;
-            p = r * P + c;
-            const int jp = J[p];
-#pragma unroll
-            for (int k = 0; k < CONN; ++k) {
-                const int rr = r + Nb<CONN>::dr(k), cc = c + Nb<CONN>::dc(k);
-                if (rr >= 1 && rr <= TS && cc >= 1 && cc <= TS) {
-                    const int q = rr * P + cc;
-                    seed |= J[q] < min(jp, I[q]);
-                }
-            }
-        }
-        wq.push(seed, p, rq);
+// Row passes (N^{+,0} left to right, then N^{-,0} right to left) of one
+// uint8 working row; one thread owns the row during the pass, so plain
+// loads can run ahead of the running value.
+__device__ __forceinline__ bool u8_row_passes(uint8_t *J, const uint8_t *I, int r) {
+    const int base = r * WU8_P + 3;
+    bool ch = false;
+    int run = J[base];
+#pragma unroll 8
+    for (int c = 1; c <= TS; ++c) {
+        const int o = J[base + c];
+        const int v = min((int)I[base + c], max(o, run));
+        if (v != o) { J[base + c] = (uint8_t)v; ch = true; }
+        run = v;
     }
-    wq.drain(rq);
+    run = J[base + TS + 1];
+#pragma unroll 8
+    for (int c = TS; c >= 1; --c) {
+        const int o = J[base + c];
+        const int v = min((int)I[base + c], max(o, run));
+        if (v != o) { J[base + c] = (uint8_t)v; ch = true; }
+        run = v;
+    }
+    return ch;
 }
 
-template <typename T, int CONN, int TS>
-__device__ void recon_tile(const KArgs &ka, const JobDesc &jd, int gt, Smem s) {
-    using G = Geo<TS>;
-    constexpr int R = G::R, P = G::P;
-    constexpr int LOW = Low<T>::v;
-    const int tid = threadIdx.x;
-    const int lt = gt - jd.tile_base;
-    const int tx = lt % jd.tiles_x, ty = lt / jd.tiles_x;
-    const int oy = ty * TS - 1, ox = tx * TS - 1;  // image coords of staged cell (0,0)
-    const T *mk = (const T *)jd.a;
-    const T *ms = (const T *)jd.b;
-    T *out = (T *)jd.out;
-    int *J = s.A;
-    const int *I = s.B;
-    volatile int *VJ = s.A;
-
-    load_sources(ka, jd, tx, ty, s);
-    if (tid < 9) s.hdr[H_FLAG + tid] = 0;
-    if (tid == 0) {
-        s.hdr[H_CNT0] = 0; s.hdr[H_CNT0 + 1] = 0; s.hdr[H_RESCAN] = 0;
-        s.hdr[H_PUSH] = 0; s.hdr[H_SPILL] = 0; s.hdr[H_RESC] = 0;
+// Row passes for int32 rows (one thread per row).
+__device__ __forceinline__ bool i32_row_passes(int *J, const int *I, int base) {
+    bool ch = false;
+    int run = J[base];
+    for (int c = 1; c <= TS; ++c) {
+        const int o = J[base + c];
+        const int v = min(I[base + c], max(o, run));
+        if (v != o) { J[base + c] = v; ch = true; }
+        run = v;
     }
+    run = J[base + TS + 1];
+    for (int c = TS; c >= 1; --c) {
+        const int o = J[base + c];
+        const int v = min(I[base + c], max(o, run));
+        if (v != o) { J[base + c] = v; ch = true; }
+        run = v;
+    }
+    return ch;
+}
+
+// Column pass (N^{0,+} downwards when DIR = +1, N^{0,-} upwards when -1) for
+// the column of this thread: one thread per column, rows in sequence.  The
+// diagonal neighbours' new values of the previous row come by warp shuffle;
+// the warp's edge lanes read the neighbouring column from shared memory,
+// where another warp may not have written it yet -- an older value, which
+// is still a valid lower bound.
+template <int CONN, int DIR, typename T>
+__device__ __forceinline__ bool column_pass(T *J, const T *I, int P, int c0) {
+    const int lane = threadIdx.x & 31;
+    const int c = threadIdx.x + 1;
+    const int r0 = DIR > 0 ? 0 : RR - 1;
+    int up = J[r0 * P + c0 + c];
+    int ul = CONN == 8 ? J[r0 * P + c0 + c - 1] : 0;
+    int ur = CONN == 8 ? J[r0 * P + c0 + c + 1] : 0;
+    bool ch = false;
+#pragma unroll 4
+    for (int s = 1; s <= TS; ++s) {
+        const int r = DIR > 0 ? s : RR - 1 - s;
+        const int i = r * P + c0 + c;
+        const int o = J[i];
+        int v = max(o, up);
+        if (CONN == 8) v = max(v, max(ul, ur));
+        v = min(v, (int)I[i]);
+        if (v != o) {
+            J[i] = (T)v;
+            ch = true;
+        }
+        up = v;
+        if (CONN == 8) {
+            int nl = __shfl_up_sync(0xffffffffu, v, 1);
+            int nr = __shfl_down_sync(0xffffffffu, v, 1);
+            if (lane == 0) nl = ((volatile T *)J)[i - 1];
+            if (lane == 31) nr = ((volatile T *)J)[i + 1];
+            ul = nl;
+            ur = nr;
+        }
+    }
+    return ch;
+}
+
+// One raster + anti-raster sweep set (rows both ways, then columns down and
+// up); returns whether any pixel changed (block-uniform).  A set that
+// changes nothing has compared every pixel with every neighbour at their
+// current values, so the tile is then stable.
+template <int CONN>
+__device__ bool sweep_set_u8(uint8_t *J, const uint8_t *I) {
+    const int t = threadIdx.x;
+    bool ch = false;
+    if (t < TS) ch |= u8_row_passes(J, I, t + 1);
     __syncthreads();
-
-    // 1. stage marker-or-current (clipped by the mask) and mask, tile + halo
-    for (int i = tid; i < R * R; i += NT) {
-        const int r = i / R, c = i - r * R;
-        const int gy = oy + r, gx = ox + c;
-        int jv = LOW, iv = LOW;
-        if (gy >= 0 && gy < jd.h && gx >= 0 && gx < jd.w) {
-            iv = ldg_val(ms + (int64_t)gy * jd.pb + gx);
-            const bool cur = s.hdr[H_SRC + region(r, R - 1) * 3 + region(c, R - 1)] != 0;
-            const int v = cur ? ldcg_val(out + (int64_t)gy * jd.po + gx)
-                              : ldcg_val(mk + (int64_t)gy * jd.pa + gx);
-            jv = min(v, iv);
-        }
-        s.A[r * P + c] = jv;
-        s.B[r * P + c] = iv;
+    if (t < TS) {
+        ch |= column_pass<CONN, +1>(J, I, WU8_P, 3);
+        ch |= column_pass<CONN, -1>(J, I, WU8_P, 3);
     }
+    return __syncthreads_or(ch) != 0;
+}
+
+template <int CONN>
+__device__ bool sweep_set_i32(int *J, const int *I) {
+    const int t = threadIdx.x;
+    bool ch = false;
+    if (t < TS) ch |= i32_row_passes(J, I, (t + 1) * BI32_W + 3);
     __syncthreads();
-
-    // 2. seed sweeps: raster (rows L->R, then columns top->bottom over the
-    //    upper neighbours) and anti-raster (rows R->L, columns bottom->top).
-    for (int sp = 0; sp < ka.sweeps; ++sp) {
-        if (tid < TS) {
-            const int r = tid + 1;
-            int run = VJ[r * P];
-            for (int c = 1; c <= TS; ++c) {
-                const int v = min(max(VJ[r * P + c], run), I[r * P + c]);
-                VJ[r * P + c] = v;
-                run = v;
-            }
-        }
-        __syncthreads();
-        if (tid < TS) {
-            const int c = tid + 1;
-            int up = VJ[c];
-            for (int r = 1; r <= TS; ++r) {
-                int v = max(VJ[r * P + c], up);
-                if (CONN == 8) v = max(v, max(VJ[(r - 1) * P + c - 1], VJ[(r - 1) * P + c + 1]));
-                v = min(v, I[r * P + c]);
-                VJ[r * P + c] = v;
-                up = v;
-            }
-        }
-        __syncthreads();
-        if (tid < TS) {
-            const int r = tid + 1;
-            int run = VJ[r * P + TS + 1];
-            for (int c = TS; c >= 1; --c) {
-                const int v = min(max(VJ[r * P + c], run), I[r * P + c]);
-                VJ[r * P + c] = v;
-                run = v;
-            }
-        }
-        __syncthreads();
-        if (tid < TS) {
-            const int c = tid + 1;
-            int dn = VJ[(TS + 1) * P + c];
-            for (int r = TS; r >= 1; --r) {
-                int v = max(VJ[r * P + c], dn);
-                if (CONN == 8) v = max(v, max(VJ[(r + 1) * P + c - 1], VJ[(r + 1) * P + c + 1]));
-                v = min(v, I[r * P + c]);
-                VJ[r * P + c] = v;
-                dn = v;
-            }
-        }
-        __syncthreads();
+    if (t < TS) {
+        ch |= column_pass<CONN, +1>(J, I, BI32_W, 3);
+        ch |= column_pass<CONN, -1>(J, I, BI32_W, 3);
     }
+    return __syncthreads_or(ch) != 0;
+}
 
-    // 3. seed scan into round queue 0
-    int *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
-    WarpQueue wq{s.WQ + (tid >> 5) * 64, 0, 0u};
-    {
-        RoundQueue rq{s.Q0, spill, s.hdr + H_CNT0, s.hdr + H_RESCAN, G::QCAP, ka.spill_cap};
-        recon_seed_scan<CONN, TS>(J, I, wq, rq);
-    }
-    __syncthreads();
-    if (tid == 0) s.hdr[H_SEEDS] = s.hdr[H_CNT0];
-
-    // 4. propagation rounds (Algorithm 5, wavefront phase)
-    int cur = 0;
-    unsigned spilled = 0, rescans = 0;
-    while (true) {
-        __syncthreads();
-        const int n_raw = s.hdr[H_CNT0 + cur];
-        const int resc = s.hdr[H_RESCAN];
-        const int n_in = min(n_raw, G::QCAP + ka.spill_cap);
-        if (n_in == 0 && !resc) break;
-        __syncthreads();
-        if (tid == 0) {
-            s.hdr[H_CNT0 + (cur ^ 1)] = 0;
-            s.hdr[H_RESCAN] = 0;
-            spilled += n_in > G::QCAP ? n_in - G::QCAP : 0;
-            rescans += resc ? 1 : 0;
+// One elementary geodesic dilation over the tile interior (each pixel takes
+// the max of its neighbourhood, clipped by the mask); every pixel that
+// changes is queued.  Afterwards every pixel that can still raise a
+// neighbour is in the queue (a pixel that did not change was seen by all its
+// neighbours, which are therefore no longer below it where the mask allows).
+// One thread per column slides a 3-row window down the tile; each pixel is
+// written only by its own thread.
+template <int CONN, int NT, typename T>
+__device__ unsigned dilate_seed(T *J, const T *I, int P, int c0, const RQ &q, const int *off) {
+    unsigned pushed = 0;
+    const int t = threadIdx.x;
+    if (t >= ((TS + 31) / 32) * 32) return 0;  // whole warps only
+    const int c = t + 1;
+    const int col = c0 + c;
+    auto hmax = [&](int r) -> int {
+        const int i = r * P + col;
+        return CONN == 8 ? max(J[i], max(J[i - 1], J[i + 1])) : (int)J[i];
+    };
+    int hp = hmax(0), hc = hmax(1);
+    for (int r = 1; r <= TS; ++r) {
+        const int hn = hmax(r + 1);
+        const int i = r * P + col;
+        const int o = J[i];
+        int m = max(hp, max(hc, hn));
+        if (CONN == 4) m = max(m, max((int)J[i - 1], (int)J[i + 1]));
+        const int v = min(m, (int)I[i]);
+        unsigned bit = 0;
+        if (v > o) {
+            J[i] = (T)v;
+            bit = 1u << 8;
         }
-        __syncthreads();
-        const int *qin_s = cur ? s.Q1 : s.Q0;
-        const int *qin_g = spill + cur * ka.spill_cap;
-        RoundQueue rq{cur ? s.Q0 : s.Q1, spill + (cur ^ 1) * ka.spill_cap,
-                      s.hdr + H_CNT0 + (cur ^ 1), s.hdr + H_RESCAN, G::QCAP, ka.spill_cap};
-        {
-            for (int base = 0; base < n_in; base += NT) {
-                const int i = base + tid;
-                const bool valid = i < n_in;
-                const int p = valid ? rq_load(qin_s, qin_g, G::QCAP, i) : (P + 1);
-                const int pr = p / P, pc = p - pr * P;
-                const int jp = valid ? VJ[p] : LOW;
+        pushed += warp_enqueue(bit, i, off, q);
+        hp = hc;
+        hc = hn;
+    }
+    return pushed;
+}
+
+// Access policy for the two value layouts.
+struct U8Grid {  // uint8 images: working copy, stride 76 bytes
+    uint8_t *J;
+    const uint8_t *I;
+    static constexpr int P = WU8_P;
+    static __device__ __forceinline__ int cell(int r, int c) { return r * P + c + 3; }
+    __device__ __forceinline__ int j(int i) const { return ((volatile uint8_t *)J)[i]; }
+    __device__ __forceinline__ int iv(int i) const { return I[i]; }
+    __device__ __forceinline__ void set(int i, int v) const { ((volatile uint8_t *)J)[i] = (uint8_t)v; }
+    // raises J[i] to v if below; true if this call raised it
+    __device__ __forceinline__ bool raise(int i, int v) const {
+        unsigned *w = (unsigned *)(J + (i & ~3));
+        const int sh = (i & 3) * 8;
+        unsigned old = *(volatile unsigned *)w;
+        while (true) {
+            if ((int)((old >> sh) & 0xFFu) >= v) return false;
+            const unsigned nw = (old & ~(0xFFu << sh)) | ((unsigned)v << sh);
+            const unsigned prev = atomicCAS(w, old, nw);
+            if (prev == old) return true;
+            old = prev;
+        }
+    }
+    __device__ __forceinline__ bool sweep(int conn) const {
+        return conn == 8 ? sweep_set_u8<8>(J, I) : sweep_set_u8<4>(J, I);
+    }
+    template <int CONN, int NT>
+    __device__ __forceinline__ unsigned dilate(const RQ &q, const int *off) const {
+        return dilate_seed<CONN, NT, uint8_t>(J, I, P, 3, q, off);
+    }
+};
+
+struct I32Grid {  // int32 images: TMA box layout, stride 72 words
+    int *J;
+    const int *I;
+    static constexpr int P = BI32_W;
+    static __device__ __forceinline__ int cell(int r, int c) { return r * P + c + 3; }
+    __device__ __forceinline__ int j(int i) const { return ((volatile int *)J)[i]; }
+    __device__ __forceinline__ int iv(int i) const { return I[i]; }
+    __device__ __forceinline__ void set(int i, int v) const { ((volatile int *)J)[i] = v; }
+    __device__ __forceinline__ bool raise(int i, int v) const { return atomicMax(J + i, v) < v; }
+    __device__ __forceinline__ bool sweep(int conn) const {
+        return conn == 8 ? sweep_set_i32<8>(J, I) : sweep_set_i32<4>(J, I);
+    }
+    template <int CONN, int NT>
+    __device__ __forceinline__ unsigned dilate(const RQ &q, const int *off) const {
+        return dilate_seed<CONN, NT, int>(J, I, P, 3, q, off);
+    }
+};
+
+template <typename G>
+__device__ __forceinline__ bool interior(int i) {
+    const int r = i / G::P, c = i - r * G::P - 3;
+    return r >= 1 && r <= TS && c >= 1 && c <= TS;
+}
+
+// Halo pixels that can raise an interior neighbour (later visits).
+template <int CONN, int NT, typename G>
+__device__ unsigned halo_seed(const G &g, const RQ &q, const int *off) {
+    unsigned pushed = 0;
+    for (int base = 0; base < 4 * (TS + 1); base += NT) {
+        const int k = base + threadIdx.x;
+        unsigned m = 0;
+        int i = 0;
+        if (k < 4 * (TS + 1)) {
+            int r, c;
+            halo_cell(k, r, c);
+            i = G::cell(r, c);
+            const int jp = g.j(i);
 #pragma unroll
-                for (int k = 0; k < CONN; ++k) {
-                    const int rr = pr + Nb<CONN>::dr(k), cc = pc + Nb<CONN>::dc(k);
-                    const int q = rr * P + cc;
-                    bool pred = false;
-                    if (valid && rr >= 1 && rr <= TS && cc >= 1 && cc <= TS) {
-                        const int v = min(jp, I[q]);
-                        if (VJ[q] < v) pred = atomicMax(J + q, v) < v;
-                    }
-                    wq.push(pred, q, rq);
+            for (int n = 0; n < CONN; ++n) {
+                const int rr = r + nb_dy(CONN, n), cc = c + nb_dx(CONN, n);
+                if (rr >= 1 && rr <= TS && cc >= 1 && cc <= TS) {
+                    const int qi = i + off[n];
+                    if (g.j(qi) < min(jp, g.iv(qi))) m = 1u << 8;
                 }
             }
-            wq.drain(rq);
         }
-        if (resc) {
-            // the in-queue of this round was truncated (items dropped): the
-            // items that fitted were processed above, which guarantees
-            // progress; the next queue is rebuilt from a full scan of the
-            // partial result (the restart rule of Section 3.2)
+        pushed += warp_enqueue(m, i, off, q);
+    }
+    return pushed;
+}
+
+template <int CONN, int NT, typename G>
+__device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t *Q0, uint16_t *Q1, bool first,
+                                const int *off) {
+    uint16_t *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
+    RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, QCAP_R, ka.spill_cap};
+    auto sweeps_then_dilate = [&](const RQ &q) -> unsigned {
+        bool changed = true;
+        for (int s = 0; s < ka.sweeps && changed; ++s) changed = g.sweep(CONN);
+        // a sweep set that changed nothing proves the tile stable
+        if (!changed && ka.sweeps > 0) return 0u;
+        return g.template dilate<CONN, NT>(q, off);
+    };
+    unsigned seeds;
+    if (first) {
+        seeds = sweeps_then_dilate(q0);
+    } else {
+        // later visit: only the halo changed.  A few entry points are
+        // cheapest as queue seeds; many mean a bulk change, which the
+        // sweeps carry further per operation than the queue.
+        seeds = halo_seed<CONN, NT>(g, q0, off);
+        __syncthreads();
+        if (hdr[H_CNT0] > ka.revisit_sweep_min) {
             __syncthreads();
-            if (tid == 0) { s.hdr[H_CNT0 + (cur ^ 1)] = 0; s.hdr[H_RESCAN] = 0; }
+            if (threadIdx.x == 0) { hdr[H_CNT0] = 0; hdr[H_RESCAN] = 0; }
             __syncthreads();
-            recon_seed_scan<CONN, TS>(J, I, wq, rq);
+            seeds = sweeps_then_dilate(q0);
         }
-        cur ^= 1;
     }
+    if ((threadIdx.x & 31) == 0) atomicAdd(hdr + H_SEEDS, (int)seeds);
+    auto proc = [&](int p) -> unsigned {
+        const int jp = g.j(p);
+        const int pr = p / G::P, pc = p - pr * G::P - 3;
+        unsigned m = 0;
+#pragma unroll
+        for (int n = 0; n < CONN; ++n) {
+            const int rr = pr + nb_dy(CONN, n), cc = pc + nb_dx(CONN, n);
+            if (rr < 1 || rr > TS || cc < 1 || cc > TS) continue;
+            const int qi = p + off[n];
+            const int v = min(jp, g.iv(qi));
+            if (g.j(qi) < v && g.raise(qi, v)) m |= 1u << n;
+        }
+        return m;
+    };
+    auto rescan = [&](const RQ &q) -> unsigned { return g.template dilate<CONN, NT>(q, off); };
+    run_rounds<NT>(hdr, Q0, Q1, QCAP_R, spill, ka.spill_cap, off, proc, rescan);
+}
 
-    // 5. store the tile
-    for (int i = tid; i < TS * TS; i += NT) {
-        const int r = i / TS + 1, c = i - (i / TS) * TS + 1;
-        const int gy = oy + r, gx = ox + c;
-        if (gy < jd.h && gx < jd.w) out[(int64_t)gy * jd.po + gx] = (T)J[r * P + c];
-    }
-    if ((tid & 31) == 0) atomicAdd(s.hdr + H_PUSH, (int)wq.pushed);
-    __syncthreads();
-    if (tid == 0) __threadfence();
-    load_sources(ka, jd, tx, ty, s);  // fresh flags for the border test
-    __syncthreads();
-
-    // 6. border test against the neighbours' current values
-    for (int i = tid; i < 4 * (TS + 1); i += NT) {
+// Border test against the neighbours' current values; flags hdr[H_FLAG..].
+template <typename T, int CONN, int NT, typename G>
+__device__ void recon_border(const JobDesc *jd, const G &g, int *hdr, int x0, int y0) {
+    const T *mk = (const T *)jd->a;
+    const T *out = (const T *)jd->out;
+    for (int k = threadIdx.x; k < 4 * (TS + 1); k += NT) {
         int r, c;
-        halo_cell<TS>(i, r, c);
-        const int gy = oy + r, gx = ox + c;
-        if (gy < 0 || gy >= jd.h || gx < 0 || gx >= jd.w) continue;
-        const int reg = region(r, R - 1) * 3 + region(c, R - 1);
-        const int iq = I[r * P + c];
-        const int v = s.hdr[H_SRC + reg] ? ldcg_val(out + (int64_t)gy * jd.po + gx)
-                                         : ldcg_val(mk + (int64_t)gy * jd.pa + gx);
+        halo_cell(k, r, c);
+        const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+        if (gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w) continue;
+        const int reg = region(r) * 3 + region(c);
+        const int i = G::cell(r, c);
+        const int iq = g.iv(i);
+        const int v = hdr[H_SRC + reg] == 1 ? (int)__ldcg(out + (int64_t)gy * jd->po + gx)
+                                            : (int)__ldcg(mk + (int64_t)gy * jd->pa + gx);
         const int jq = min(v, iq);
         bool need = false;
 #pragma unroll
-        for (int k = 0; k < CONN; ++k) {
-            const int pr = r + Nb<CONN>::dr(k), pc = c + Nb<CONN>::dc(k);
-            if (pr >= 1 && pr <= TS && pc >= 1 && pc <= TS) need |= jq < min(J[pr * P + pc], iq);
+        for (int n = 0; n < CONN; ++n) {
+            const int pr = r + nb_dy(CONN, n), pc = c + nb_dx(CONN, n);
+            if (pr >= 1 && pr <= TS && pc >= 1 && pc <= TS) need |= jq < min(g.j(G::cell(pr, pc)), iq);
         }
-        if (need) s.hdr[H_FLAG + reg] = 1;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        s.hdr[H_SPILL] = (int)spilled;
-        s.hdr[H_RESC] = (int)rescans;
-        finish_tile(ka, jd, gt, tx, ty, s);
+        if (need) hdr[H_FLAG + reg] = 1;
     }
 }
 
+template <int CONN, int NT>
+__device__ bool recon_u8_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, uint32_t &phase,
+                               unsigned long long deadline) {
+    int *hdr = (int *)sm;
+    uint64_t *bar = (uint64_t *)(sm + 256);
+    uint8_t *JW = (uint8_t *)(sm + RU8_JW);
+    uint8_t *IW = (uint8_t *)(sm + RU8_IW);
+    uint8_t *IB = (uint8_t *)(sm + RU8_U);
+    uint8_t *JBm = IB + BU8_PAD;      // marker box
+    uint8_t *JBo = IB + 2 * BU8_PAD;  // current-result box
+    uint16_t *Q0 = (uint16_t *)(sm + RU8_U), *Q1 = Q0 + QCAP_R;
+    const int tid = threadIdx.x;
+    const int lt = gt - jd->tile_base, tx = lt % jd->tiles_x, ty = lt / jd->tiles_x;
+    const int x0 = tx * TS, y0 = ty * TS;
+    const uint8_t *mk = (const uint8_t *)jd->a, *ms = (const uint8_t *)jd->b;
+    uint8_t *out = (uint8_t *)jd->out;
+
+    load_sources(ka, jd, tx, ty, hdr);
+    begin_visit(hdr);
+    make_offsets<CONN, WU8_P>(hdr);
+    __syncthreads();
+    int need_m = 0, need_o = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        need_m |= hdr[H_SRC + k] == 0;
+        need_o |= hdr[H_SRC + k] == 1;
+    }
+    const bool first = hdr[H_SRC + 4] == 0;
+
+    // 1. stage the mask, marker and/or current-result boxes
+    if (jd->use_tma) {
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, BU8_BYTES * (1 + need_m + need_o));
+            tma_load_2d(IB, &jd->tm[1], x0 - 16, y0 - 1, bar);
+            if (need_m) tma_load_2d(JBm, &jd->tm[0], x0 - 16, y0 - 1, bar);
+            if (need_o) tma_load_2d(JBo, &jd->tm[2], x0 - 16, y0 - 1, bar);
+        }
+        if (!wait_boxes(bar, phase, deadline, ka.ctl)) return false;
+    } else {
+        stage_plain<uint8_t, BU8_W>(IB, ms, jd->pb, jd->h, jd->w, x0 - 16, y0 - 1, NT);
+        if (need_m) stage_plain<uint8_t, BU8_W>(JBm, mk, jd->pa, jd->h, jd->w, x0 - 16, y0 - 1, NT);
+        if (need_o) stage_plain<uint8_t, BU8_W>(JBo, out, jd->po, jd->h, jd->w, x0 - 16, y0 - 1, NT);
+        __syncthreads();
+    }
+    // working copy (word copies; each word lies in one column region, words
+    // 0 and 17 being the left / right halo columns).  Cells outside the
+    // image are zero in both J and I (zero fill) and so never raise or get
+    // raised.
+    {
+        const uint32_t *I32 = (const uint32_t *)IB, *M32 = (const uint32_t *)JBm, *O32 = (const uint32_t *)JBo;
+        uint32_t *JW32 = (uint32_t *)JW, *IW32 = (uint32_t *)IW;
+        for (int i = tid; i < RR * 19; i += NT) {
+            const int r = i / 19, k = i - r * 19;
+            if (k == 18) {
+                JW32[i] = 0;
+                IW32[i] = 0;
+                continue;
+            }
+            const int reg = region(r) * 3 + (k == 0 ? 0 : (k == 17 ? 2 : 1));
+            IW32[i] = I32[r * 24 + 3 + k];
+            JW32[i] = hdr[H_SRC + reg] == 1 ? O32[r * 24 + 3 + k] : M32[r * 24 + 3 + k];
+        }
+    }
+    __syncthreads();
+    // clip marker values by the mask where no later step does it: the halo
+    // ring always (halo pixels are sources only), the interior on a first
+    // visit without sweeps (the first row pass clips every interior pixel)
+    for (int k = tid; k < 4 * (TS + 1); k += NT) {
+        int r, c;
+        halo_cell(k, r, c);
+        const int i = U8Grid::cell(r, c);
+        if (JW[i] > IW[i]) JW[i] = IW[i];
+    }
+    if (first && ka.sweeps == 0)
+        for (int k = tid; k < TS * TS; k += NT) {
+            const int i = U8Grid::cell(k / TS + 1, k % TS + 1);
+            if (JW[i] > IW[i]) JW[i] = IW[i];
+        }
+    __syncthreads();
+
+    U8Grid g{JW, IW};
+    const int *off = hdr + H_OFF;
+
+    // 2. sweeps, 3. seeds + propagation
+    recon_propagate<CONN, NT>(ka, g, hdr, Q0, Q1, first, off);
+    __syncthreads();
+
+    // 4. store the interior rows (16-byte vector stores when aligned)
+    {
+        const bool vec = jd->use_tma != 0;  // TMA maps imply 16-byte aligned base and pitch
+        for (int i = tid; i < TS * 4; i += NT) {
+            const int r = i >> 2, q = i & 3;
+            const int gy = y0 + r, gx = x0 + q * 16;
+            if (gy >= jd->h || gx >= jd->w) continue;
+            const uint32_t *src = (const uint32_t *)(JW + (r + 1) * WU8_P + 4 + q * 16);
+            uint8_t *dst = out + (int64_t)gy * jd->po + gx;
+            if (vec && gx + 16 <= jd->w) {
+                *(uint4 *)dst = make_uint4(src[0], src[1], src[2], src[3]);
+            } else {
+                const int n = min(16, jd->w - gx);
+                for (int b = 0; b < n; ++b) dst[b] = JW[(r + 1) * WU8_P + 4 + q * 16 + b];
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) __threadfence();
+    load_sources(ka, jd, tx, ty, hdr);  // fresh states for the border test
+    __syncthreads();
+    recon_border<uint8_t, CONN, NT>(jd, g, hdr, x0, y0);
+    __syncthreads();
+    if (tid == 0) finish_tile(ka, jd, gt, tx, ty, hdr);
+    return true;
+}
+
+template <int CONN, int NT>
+__device__ bool recon_i32_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, uint32_t &phase,
+                                unsigned long long deadline) {
+    int *hdr = (int *)sm;
+    uint64_t *bar = (uint64_t *)(sm + 256);
+    int *JB = (int *)(sm + RI32_J);
+    int *IB = (int *)(sm + RI32_I);
+    int *OB = (int *)(sm + RI32_U);  // second J source, later the queues
+    uint16_t *Q0 = (uint16_t *)(sm + RI32_U), *Q1 = Q0 + QCAP_R;
+    const int tid = threadIdx.x;
+    const int lt = gt - jd->tile_base, tx = lt % jd->tiles_x, ty = lt / jd->tiles_x;
+    const int x0 = tx * TS, y0 = ty * TS;
+    const int *mk = (const int *)jd->a, *ms = (const int *)jd->b;
+    int *out = (int *)jd->out;
+
+    load_sources(ka, jd, tx, ty, hdr);
+    begin_visit(hdr);
+    make_offsets<CONN, BI32_W>(hdr);
+    __syncthreads();
+    int need_m = 0, need_o = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        need_m |= hdr[H_SRC + k] == 0;
+        need_o |= hdr[H_SRC + k] == 1;
+    }
+    const bool first = hdr[H_SRC + 4] == 0;
+    int *odst = need_m ? OB : JB;  // marker -> JB; current result -> OB, or JB alone
+    if (jd->use_tma) {
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, BI32_BYTES * (1 + need_m + need_o));
+            tma_load_2d(IB, &jd->tm[1], x0 - 4, y0 - 1, bar);
+            if (need_m) tma_load_2d(JB, &jd->tm[0], x0 - 4, y0 - 1, bar);
+            if (need_o) tma_load_2d(odst, &jd->tm[2], x0 - 4, y0 - 1, bar);
+        }
+        if (!wait_boxes(bar, phase, deadline, ka.ctl)) return false;
+    } else {
+        stage_plain<int, BI32_W>(IB, ms, jd->pb, jd->h, jd->w, x0 - 4, y0 - 1, NT);
+        if (need_m) stage_plain<int, BI32_W>(JB, mk, jd->pa, jd->h, jd->w, x0 - 4, y0 - 1, NT);
+        if (need_o) stage_plain<int, BI32_W>(odst, out, jd->po, jd->h, jd->w, x0 - 4, y0 - 1, NT);
+        __syncthreads();
+    }
+    // merge the sources, clip by the mask, and give cells outside the image
+    // the lowest value (they then never raise or get raised)
+    for (int i = tid; i < RR * BI32_W; i += NT) {
+        const int r = i / BI32_W, c = i - r * BI32_W - 3;
+        const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+        if (c < 0 || c >= RR || gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w) {
+            JB[i] = INT_MIN;
+            IB[i] = INT_MIN;
+            continue;
+        }
+        const int reg = region(r) * 3 + region(c);
+        const int v = (need_m && need_o && hdr[H_SRC + reg] == 1) ? OB[i] : JB[i];
+        JB[i] = min(v, IB[i]);
+    }
+    __syncthreads();
+
+    I32Grid g{JB, IB};
+    const int *off = hdr + H_OFF;
+    recon_propagate<CONN, NT>(ka, g, hdr, Q0, Q1, first, off);
+    __syncthreads();
+    for (int i = tid; i < TS * TS; i += NT) {
+        const int r = i / TS, c = i - r * TS;
+        const int gy = y0 + r, gx = x0 + c;
+        if (gy < jd->h && gx < jd->w) out[(int64_t)gy * jd->po + gx] = JB[I32Grid::cell(r + 1, c + 1)];
+    }
+    __syncthreads();
+    if (tid == 0) __threadfence();
+    load_sources(ka, jd, tx, ty, hdr);
+    __syncthreads();
+    recon_border<int, CONN, NT>(jd, g, hdr, x0, y0);
+    __syncthreads();
+    if (tid == 0) finish_tile(ka, jd, gt, tx, ty, hdr);
+    return true;
+}
+
 // =====================================================================
-// Distance transform by nearest-feature propagation (Section 2.2;
-// Algorithms 3 and 6).  Shared memory holds the Voronoi assignment VR as
-// packed image coordinates (y << 16 | x); 0xFFFFFFFF is the virtual 'inf'
-// pixel, farther than any real pixel.
+// Distance transform (Section 2.2; Algorithms 3 and 6).  Each staged pixel
+// holds one 64-bit word: squared distance to its assigned feature in the
+// high half, the feature's packed coordinates (y << 16 | x) in the low half;
+// all ones is the virtual 'inf' pixel.  Propagating feature f to q is one
+// atomicMin of (d2(q, f) << 32 | f): the word only decreases, so q takes f
+// exactly when f is strictly closer, or equally close with smaller
+// coordinates (a fixed tie rule in place of the arrival order).
 // =====================================================================
 
-enum : unsigned { VR_INF = 0xFFFFFFFFu };
+constexpr unsigned long long W_INF = ~0ull;
 
 __device__ __forceinline__ unsigned pack_yx(int y, int x) { return ((unsigned)y << 16) | (unsigned)x; }
 
-// squared distance from (y, x) to packed feature f; VR_INF for 'inf'
-__device__ __forceinline__ unsigned d2(int y, int x, unsigned f) {
-    if (f == VR_INF) return VR_INF;
+__device__ __forceinline__ unsigned long long cand(int y, int x, unsigned f) {
     const int dy = y - (int)(f >> 16), dx = x - (int)(f & 0xFFFFu);
-    return (unsigned)(dy * dy + dx * dx);
+    return ((unsigned long long)(unsigned)(dy * dy + dx * dx) << 32) | f;
 }
 
-__device__ __forceinline__ bool is_feature(uint8_t b, int flags) {
-    return (flags & 1) ? b != 0 : b == 0;
-}
+__device__ __forceinline__ bool is_feature(uint8_t b, int flags) { return (flags & 1) ? b != 0 : b == 0; }
 
-// current VR of image pixel (gy, gx): from the stored result of a visited
-// tile, else from the binary input (Algorithm 6 initialisation)
-__device__ __forceinline__ unsigned vr_fetch(const JobDesc &jd, bool visited, int gy, int gx) {
+// current word of image pixel (gy, gx) read from global memory
+__device__ __forceinline__ unsigned long long w_fetch(const JobDesc *jd, bool visited, int gy, int gx) {
     if (visited) {
-        const int idx = __ldcg(jd.nearest + (int64_t)gy * jd.w + gx);
-        if (idx < 0) return VR_INF;
-        const int fy = idx / jd.w;
-        return pack_yx(fy, idx - fy * jd.w);
+        const int idx = __ldcg(jd->nearest + (int64_t)gy * jd->w + gx);
+        if (idx < 0) return W_INF;
+        const int fy = idx / jd->w;
+        return cand(gy, gx, pack_yx(fy, idx - fy * jd->w));
     }
-    const uint8_t b = __ldg((const uint8_t *)jd.a + (int64_t)gy * jd.pa + gx);
-    return is_feature(b, jd.flags) ? pack_yx(gy, gx) : VR_INF;
+    const uint8_t b = __ldcg((const uint8_t *)jd->a + (int64_t)gy * jd->pa + gx);
+    return is_feature(b, jd->flags) ? cand(gy, gx, pack_yx(gy, gx)) : W_INF;
 }
 
-template <int TS>
-__device__ void edt_seed_scan(const unsigned *V, int oy, int ox, WarpQueue &wq, const RoundQueue &rq) {
-    using G = Geo<TS>;
-    constexpr int R = G::R, P = G::P;
-    for (int base = 0; base < R * R; base += NT) {
-        const int i = base + threadIdx.x;
-        bool seed = false;
-        int p = 0;
-        if (i < R * R) {
-            const int r = i / R, c = i - r * R;
-            p = r * P + c;
-            const unsigned f = V[p];
-            if (f != VR_INF) {
+// Can the feature f of cell (pr, pc) improve its interior neighbour n?  With
+// commit, performs the update and reports whether this call made it.
+__device__ __forceinline__ bool edt_try(unsigned long long *W, int oy, int ox, int pr, int pc, unsigned f, int n,
+                                        bool commit) {
+    const int rr = pr + nb_dy(8, n), cc = pc + nb_dx(8, n);
+    if (rr < 1 || rr > TS || cc < 1 || cc > TS) return false;
+    const int qi = rr * WE_P + cc;
+    const unsigned long long wq = ((volatile unsigned long long *)W)[qi];
+    if ((wq >> 32) == 0) return false;  // a feature is its own nearest feature
+    const unsigned long long cv = cand(oy + rr, ox + cc, f);
+    if (cv >= wq) return false;
+    if (!commit) return true;
+    return atomicMin(W + qi, cv) > cv;
+}
+
+template <int NT>
+__device__ unsigned edt_seed_scan(unsigned long long *W, int oy, int ox, const RQ &q, bool all, const int *off) {
+    unsigned pushed = 0;
+    const int ncell = all ? RR * RR : 4 * (TS + 1);
+    for (int base = 0; base < ncell; base += NT) {
+        const int k = base + threadIdx.x;
+        unsigned m = 0;
+        int i = 0;
+        if (k < ncell) {
+            int r, c;
+            if (all) { r = k / RR; c = k - r * RR; }
+            else halo_cell(k, r, c);
+            i = r * WE_P + c;
+            const unsigned long long w = W[i];
+            if (w != W_INF) {
+                const unsigned f = (unsigned)w;
+                if ((w >> 32) == 0) {
+                    // a feature improves exactly its interior neighbours
+                    // that are not features themselves
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int rr = r + Nb<8>::dr(k), cc = c + Nb<8>::dc(k);
-                    if (rr >= 1 && rr <= TS && cc >= 1 && cc <= TS) {
-                        const int y = oy + rr, x = ox + cc;
-                        seed |= d2(y, x, f) < d2(y, x, V[rr * P + cc]);
+                    for (int n = 0; n < 8; ++n) {
+                        const int rr = r + nb_dy(8, n), cc = c + nb_dx(8, n);
+                        if (rr >= 1 && rr <= TS && cc >= 1 && cc <= TS && (W[rr * WE_P + cc] >> 32) != 0)
+                            m = 1u << 8;
                     }
+                } else {
+#pragma unroll
+                    for (int n = 0; n < 8; ++n)
+                        if (edt_try(W, oy, ox, r, c, f, n, false)) m = 1u << 8;
                 }
             }
         }
-        wq.push(seed, p, rq);
+        pushed += warp_enqueue(m, i, off, q);
     }
-    wq.drain(rq);
+    return pushed;
 }
 
-template <int TS>
-__device__ void edt_tile(const KArgs &ka, const JobDesc &jd, int gt, Smem s) {
-    using G = Geo<TS>;
-    constexpr int R = G::R, P = G::P;
+template <int NT>
+__device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, uint32_t &phase,
+                          unsigned long long deadline) {
+    int *hdr = (int *)sm;
+    uint64_t *bar = (uint64_t *)(sm + 256);
+    unsigned long long *W = (unsigned long long *)(sm + E_W);
+    uint8_t *BB = (uint8_t *)(sm + E_U);
+    int *NB = (int *)(sm + E_U + BU8_PAD);
+    uint16_t *Q0 = (uint16_t *)(sm + E_U), *Q1 = Q0 + QCAP_E;
     const int tid = threadIdx.x;
-    const int lt = gt - jd.tile_base;
-    const int tx = lt % jd.tiles_x, ty = lt / jd.tiles_x;
-    const int oy = ty * TS - 1, ox = tx * TS - 1;
-    unsigned *V = (unsigned *)s.A;
-    volatile unsigned *VV = V;
+    const int lt = gt - jd->tile_base, tx = lt % jd->tiles_x, ty = lt / jd->tiles_x;
+    const int x0 = tx * TS, y0 = ty * TS;
+    const int oy = y0 - 1, ox = x0 - 1;
 
-    load_sources(ka, jd, tx, ty, s);
-    if (tid < 9) s.hdr[H_FLAG + tid] = 0;
-    if (tid == 0) {
-        s.hdr[H_CNT0] = 0; s.hdr[H_CNT0 + 1] = 0; s.hdr[H_RESCAN] = 0;
-        s.hdr[H_PUSH] = 0; s.hdr[H_SPILL] = 0; s.hdr[H_RESC] = 0;
-    }
+    load_sources(ka, jd, tx, ty, hdr);
+    begin_visit(hdr);
+    make_offsets<8, WE_P>(hdr);
     __syncthreads();
-
-    // 1. stage VR of tile + halo
-    for (int i = tid; i < R * R; i += NT) {
-        const int r = i / R, c = i - r * R;
-        const int gy = oy + r, gx = ox + c;
-        unsigned v = VR_INF;
-        if (gy >= 0 && gy < jd.h && gx >= 0 && gx < jd.w) {
-            const bool visited = s.hdr[H_SRC + region(r, R - 1) * 3 + region(c, R - 1)] != 0;
-            v = vr_fetch(jd, visited, gy, gx);
-        }
-        V[r * P + c] = v;
-    }
-    __syncthreads();
-
-    // 2. seed scan (Algorithm 6 lines 2-5, generalised to partial results)
-    int *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
-    WarpQueue wq{s.WQ + (tid >> 5) * 64, 0, 0u};
-    {
-        RoundQueue rq{s.Q0, spill, s.hdr + H_CNT0, s.hdr + H_RESCAN, G::QCAP, ka.spill_cap};
-        edt_seed_scan<TS>(V, oy, ox, wq, rq);
-    }
-    __syncthreads();
-    if (tid == 0) s.hdr[H_SEEDS] = s.hdr[H_CNT0];
-
-    // 3. propagation rounds with CAS retry (Algorithm 6, wavefront phase)
-    int cur = 0;
-    unsigned spilled = 0, rescans = 0;
-    while (true) {
-        __syncthreads();
-        const int n_raw = s.hdr[H_CNT0 + cur];
-        const int resc = s.hdr[H_RESCAN];
-        const int n_in = min(n_raw, G::QCAP + ka.spill_cap);
-        if (n_in == 0 && !resc) break;
-        __syncthreads();
-        if (tid == 0) {
-            s.hdr[H_CNT0 + (cur ^ 1)] = 0;
-            s.hdr[H_RESCAN] = 0;
-            spilled += n_in > G::QCAP ? n_in - G::QCAP : 0;
-            rescans += resc ? 1 : 0;
-        }
-        __syncthreads();
-        const int *qin_s = cur ? s.Q1 : s.Q0;
-        const int *qin_g = spill + cur * ka.spill_cap;
-        RoundQueue rq{cur ? s.Q0 : s.Q1, spill + (cur ^ 1) * ka.spill_cap,
-                      s.hdr + H_CNT0 + (cur ^ 1), s.hdr + H_RESCAN, G::QCAP, ka.spill_cap};
-        {
-            for (int base = 0; base < n_in; base += NT) {
-                const int i = base + tid;
-                const bool valid = i < n_in;
-                const int p = valid ? rq_load(qin_s, qin_g, G::QCAP, i) : (P + 1);
-                const int pr = p / P, pc = p - pr * P;
-                const unsigned f = valid ? VV[p] : VR_INF;
+    int need_b = 0, need_n = 0;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int rr = pr + Nb<8>::dr(k), cc = pc + Nb<8>::dc(k);
-                    const int q = rr * P + cc;
-                    bool pred = false;
-                    if (f != VR_INF && rr >= 1 && rr <= TS && cc >= 1 && cc <= TS) {
-                        const int y = oy + rr, x = ox + cc;
-                        const unsigned dn = d2(y, x, f);
-                        unsigned cq = VV[q];
-                        while (dn < d2(y, x, cq)) {
-                            const unsigned old = atomicCAS(V + q, cq, f);
-                            if (old == cq) { pred = true; break; }
-                            cq = old;
-                        }
-                    }
-                    wq.push(pred, q, rq);
-                }
-            }
-            wq.drain(rq);
-        }
-        if (resc) {  // truncated in-queue: processed what fitted, now rescan
-            __syncthreads();
-            if (tid == 0) { s.hdr[H_CNT0 + (cur ^ 1)] = 0; s.hdr[H_RESCAN] = 0; }
-            __syncthreads();
-            edt_seed_scan<TS>(V, oy, ox, wq, rq);
-        }
-        cur ^= 1;
+    for (int k = 0; k < 9; ++k) {
+        need_b |= hdr[H_SRC + k] == 0;
+        need_n |= hdr[H_SRC + k] == 1;
     }
-
-    // 4. store VR (as linear index) and the squared distance (Algorithm 6,
-    //    final loop)
-    for (int i = tid; i < TS * TS; i += NT) {
-        const int r = i / TS + 1, c = i - (i / TS) * TS + 1;
+    const bool first = hdr[H_SRC + 4] == 0;
+    if (jd->use_tma) {
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, need_b * BU8_BYTES + need_n * BI32_BYTES);
+            if (need_b) tma_load_2d(BB, &jd->tm[0], x0 - 16, oy, bar);
+            if (need_n) tma_load_2d(NB, &jd->tm[2], x0 - 4, oy, bar);
+        }
+        if (!wait_boxes(bar, phase, deadline, ka.ctl)) return false;
+    } else {
+        if (need_b)
+            stage_plain<uint8_t, BU8_W>(BB, (const uint8_t *)jd->a, jd->pa, jd->h, jd->w, x0 - 16, oy, NT);
+        if (need_n) stage_plain<int, BI32_W>(NB, jd->nearest, jd->w, jd->h, jd->w, x0 - 4, oy, NT);
+        __syncthreads();
+    }
+    // 1. working words of tile + halo
+    for (int i = tid; i < RR * RR; i += NT) {
+        const int r = i / RR, c = i - r * RR;
         const int gy = oy + r, gx = ox + c;
-        if (gy < jd.h && gx < jd.w) {
-            const unsigned f = V[r * P + c];
-            const int64_t o = (int64_t)gy * jd.w + gx;
-            if (f == VR_INF) {
-                jd.nearest[o] = -1;
-                jd.sqdist[o] = INT_MAX;
-            } else {
-                jd.nearest[o] = (int)(f >> 16) * jd.w + (int)(f & 0xFFFFu);
-                jd.sqdist[o] = (int)d2(gy, gx, f);
+        unsigned long long v = W_INF;
+        if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
+            if (hdr[H_SRC + region(r) * 3 + region(c)] == 1) {
+                const int idx = NB[r * BI32_W + c + 3];
+                if (idx >= 0) {
+                    const int fy = idx / jd->w;
+                    v = cand(gy, gx, pack_yx(fy, idx - fy * jd->w));
+                }
+            } else if (is_feature(BB[r * BU8_W + c + 15], jd->flags)) {
+                v = cand(gy, gx, pack_yx(gy, gx));
             }
         }
+        W[r * WE_P + c] = v;
     }
-    if ((tid & 31) == 0) atomicAdd(s.hdr + H_PUSH, (int)wq.pushed);
+    __syncthreads();
+    const int *off = hdr + H_OFF;
+
+    // 2. seeds: every staged pixel that can improve an interior neighbour on
+    //    a first visit, only the halo on later visits
+    uint16_t *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
+    RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, QCAP_E, ka.spill_cap};
+    const unsigned seeds = edt_seed_scan<NT>(W, oy, ox, q0, first, off);
+    if ((tid & 31) == 0) atomicAdd(hdr + H_SEEDS, (int)seeds);
+
+    // 3. propagation rounds
+    auto proc = [&](int p) -> unsigned {
+        const unsigned long long w = ((volatile unsigned long long *)W)[p];
+        if (w == W_INF) return 0u;
+        const unsigned f = (unsigned)w;
+        const int pr = p / WE_P, pc = p - pr * WE_P;
+        unsigned m = 0;
+#pragma unroll
+        for (int n = 0; n < 8; ++n)
+            if (edt_try(W, oy, ox, pr, pc, f, n, true)) m |= 1u << n;
+        return m;
+    };
+    auto rescan = [&](const RQ &q) -> unsigned { return edt_seed_scan<NT>(W, oy, ox, q, true, off); };
+    run_rounds<NT>(hdr, Q0, Q1, QCAP_E, spill, ka.spill_cap, off, proc, rescan);
+    __syncthreads();
+
+    // 4. store nearest (linear index) and squared distance
+    for (int i = tid; i < TS * TS; i += NT) {
+        const int r = i / TS, c = i - r * TS;
+        const int gy = y0 + r, gx = x0 + c;
+        if (gy >= jd->h || gx >= jd->w) continue;
+        const unsigned long long w = W[(r + 1) * WE_P + c + 1];
+        const int64_t o = (int64_t)gy * jd->w + gx;
+        if (w == W_INF) {
+            jd->nearest[o] = -1;
+            jd->sqdist[o] = INT_MAX;
+        } else {
+            const unsigned f = (unsigned)w;
+            jd->nearest[o] = (int)(f >> 16) * jd->w + (int)(f & 0xFFFFu);
+            jd->sqdist[o] = (int)(w >> 32);
+        }
+    }
     __syncthreads();
     if (tid == 0) __threadfence();
-    load_sources(ka, jd, tx, ty, s);
+    load_sources(ka, jd, tx, ty, hdr);
     __syncthreads();
 
-    // 5. border test
-    for (int i = tid; i < 4 * (TS + 1); i += NT) {
+    // 5. border test (strict distance rule across tiles)
+    for (int k = tid; k < 4 * (TS + 1); k += NT) {
         int r, c;
-        halo_cell<TS>(i, r, c);
+        halo_cell(k, r, c);
         const int gy = oy + r, gx = ox + c;
-        if (gy < 0 || gy >= jd.h || gx < 0 || gx >= jd.w) continue;
-        const int reg = region(r, R - 1) * 3 + region(c, R - 1);
-        const unsigned cq = vr_fetch(jd, s.hdr[H_SRC + reg] != 0, gy, gx);
-        const unsigned dq = d2(gy, gx, cq);
+        if (gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w) continue;
+        const int reg = region(r) * 3 + region(c);
+        const unsigned dq = (unsigned)(w_fetch(jd, hdr[H_SRC + reg] == 1, gy, gx) >> 32);
         bool need = false;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int pr = r + Nb<8>::dr(k), pc = c + Nb<8>::dc(k);
-            if (pr >= 1 && pr <= TS && pc >= 1 && pc <= TS) need |= d2(gy, gx, V[pr * P + pc]) < dq;
+        for (int n = 0; n < 8; ++n) {
+            const int pr = r + nb_dy(8, n), pc = c + nb_dx(8, n);
+            if (pr < 1 || pr > TS || pc < 1 || pc > TS) continue;
+            const unsigned long long wp = W[pr * WE_P + pc];
+            if (wp != W_INF && (unsigned)(cand(gy, gx, (unsigned)wp) >> 32) < dq) need = true;
         }
-        if (need) s.hdr[H_FLAG + reg] = 1;
+        if (need) hdr[H_FLAG + reg] = 1;
     }
     __syncthreads();
-    if (tid == 0) {
-        s.hdr[H_SPILL] = (int)spilled;
-        s.hdr[H_RESC] = (int)rescans;
-        finish_tile(ka, jd, gt, tx, ty, s);
-    }
+    if (tid == 0) finish_tile(ka, jd, gt, tx, ty, hdr);
+    return true;
 }
 
 // =====================================================================
 // kernels
 // =====================================================================
 
-template <int TS>
-__global__ void __launch_bounds__(NT) persistent_kernel(const __grid_constant__ KArgs ka) {
-    extern __shared__ int smem_raw[];
-    Smem s = carve<TS>(smem_raw);
+template <int FAM>
+__global__ void __launch_bounds__(FAM_NT[FAM]) persistent_kernel(const __grid_constant__ KArgs ka) {
+    constexpr int NT = FAM_NT[FAM];
+    extern __shared__ __align__(128) char smem[];
+    int *hdr = (int *)smem;
+    uint64_t *bar = (uint64_t *)(smem + 256);
     if (ld_volatile(&ka.ctl->done)) return;
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
     const unsigned long long deadline = globaltimer_ns() + ka.timeout_ns;
+    unsigned long long t_wait = 0, t_visit = 0;
     while (true) {
-        if (threadIdx.x == 0) s.hdr[H_TILE] = tq_claim(ka.tq, ka.ctl, deadline);
+        unsigned long long t0 = 0;
+        if (threadIdx.x == 0) {
+            t0 = globaltimer_ns();
+            hdr[H_TILE] = tq_claim(ka.tq, ka.ctl, deadline);
+            const unsigned long long t1 = globaltimer_ns();
+            t_wait += t1 - t0;
+            t0 = t1;
+        }
         __syncthreads();
-        const int t = s.hdr[H_TILE];
+        const int t = hdr[H_TILE];
         if (t < 0) break;
-        const JobDesc jd = job_of(ka, t);
-        if (jd.op == OP_RECON) {
-            if (jd.dtype == DT_U8) {
-                if (jd.conn == 8) recon_tile<uint8_t, 8, TS>(ka, jd, t, s);
-                else recon_tile<uint8_t, 4, TS>(ka, jd, t, s);
-            } else {
-                if (jd.conn == 8) recon_tile<int32_t, 8, TS>(ka, jd, t, s);
-                else recon_tile<int32_t, 4, TS>(ka, jd, t, s);
+        const JobDesc *jd = job_of(ka, t);
+        bool ok = true;
+        if (jd->op == OP_RECON) {
+            if constexpr (FAM == FAM_RECON_U8 || FAM == FAM_MIXED) {
+                if (jd->dtype == DT_U8)
+                    ok = jd->conn == 8 ? recon_u8_visit<8, NT>(ka, jd, t, smem, phase, deadline)
+                                       : recon_u8_visit<4, NT>(ka, jd, t, smem, phase, deadline);
+            }
+            if constexpr (FAM == FAM_RECON_I32 || FAM == FAM_MIXED) {
+                if (jd->dtype == DT_I32)
+                    ok = jd->conn == 8 ? recon_i32_visit<8, NT>(ka, jd, t, smem, phase, deadline)
+                                       : recon_i32_visit<4, NT>(ka, jd, t, smem, phase, deadline);
             }
         } else {
-            edt_tile<TS>(ka, jd, t, s);
+            if constexpr (FAM == FAM_EDT || FAM == FAM_MIXED) ok = edt_visit<NT>(ka, jd, t, smem, phase, deadline);
         }
+        if (!ok) break;  // timeout raised; the host reports it
         if (threadIdx.x == 0) {
+            t_visit += globaltimer_ns() - t0;
             atomicAdd(&ka.ctl->tiles_processed, 1ull);
-            atomicAdd(&ka.ctl->seeds, (unsigned long long)s.hdr[H_SEEDS]);
-            atomicAdd(&ka.ctl->pushes, (unsigned long long)s.hdr[H_PUSH]);
-            atomicAdd(&ka.ctl->spills, (unsigned long long)s.hdr[H_SPILL]);
-            atomicAdd(&ka.ctl->rescans, (unsigned long long)s.hdr[H_RESC]);
+            atomicAdd(&ka.ctl->seeds, (unsigned long long)hdr[H_SEEDS]);
+            atomicAdd(&ka.ctl->pushes, (unsigned long long)hdr[H_PUSH]);
+            atomicAdd(&ka.ctl->spills, (unsigned long long)hdr[H_SPILL]);
+            atomicAdd(&ka.ctl->rescans, (unsigned long long)hdr[H_RESC]);
+            atomicAdd(&ka.ctl->rounds, (unsigned long long)hdr[H_ROUNDS]);
             __threadfence();
             atomicSub(ka.tq.pending, 1);
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0) {
+        atomicAdd(&ka.ctl->wait_ns, t_wait);
+        atomicAdd(&ka.ctl->visit_ns, t_visit);
+    }
 }
 
 // Slot of tile t in the initial queue: colour class (x mod 2, y mod 2)
 // first, so that tiles visited at the same time are never adjacent.
-__device__ __forceinline__ int initial_slot(const JobDesc &jd, int t) {
-    const int lt = t - jd.tile_base;
-    const int x = lt % jd.tiles_x, y = lt / jd.tiles_x;
+__device__ __forceinline__ int initial_slot(const JobDesc *jd, int t) {
+    const int lt = t - jd->tile_base;
+    const int x = lt % jd->tiles_x, y = lt / jd->tiles_x;
     const int a = x & 1, b = y & 1;
-    const int nx = (jd.tiles_x - a + 1) >> 1;
-    return jd.color_base[b * 2 + a] + (y >> 1) * nx + (x >> 1);
+    const int nx = (jd->tiles_x - a + 1) >> 1;
+    return jd->color_base[b * 2 + a] + (y >> 1) * nx + (x >> 1);
 }
 
 __global__ void fill_queue_kernel(const __grid_constant__ KArgs ka, int first) {
@@ -632,8 +1086,7 @@ __global__ void fill_queue_kernel(const __grid_constant__ KArgs ka, int first) {
     const int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)ka.tq.cap; i += stride) {
         if (i < ka.ntiles) {
-            const JobDesc jd = job_of(ka, i);
-            ka.tq.slots[initial_slot(jd, i)] = i;
+            ka.tq.slots[initial_slot(job_of(ka, i), i)] = i;
             ka.tq.state[i] = TS_QUEUED;
             if (first) ka.tq.visited[i] = 0;
         } else {
@@ -681,51 +1134,46 @@ __global__ void decide_kernel(const __grid_constant__ KArgs ka, int final_step) 
     }
 }
 
-int smem_bytes(int tile) {
-    switch (tile) {
-        case 32: return Geo<32>::WORDS * 4;
-        case 64: return Geo<64>::WORDS * 4;
-        default: return -1;
-    }
+int family_threads(int fam) { return (fam >= 0 && fam < FAM_COUNT) ? FAM_NT[fam] : -1; }
+int family_smem(int fam) { return (fam >= 0 && fam < FAM_COUNT) ? FAM_SMEM[fam] : -1; }
+
+template <int FAM>
+static cudaError_t occ(int *n) {
+    cudaError_t e = cudaFuncSetAttribute(persistent_kernel<FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         FAM_SMEM[FAM]);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, persistent_kernel<FAM>, FAM_NT[FAM], FAM_SMEM[FAM]);
 }
 
-template <int TS>
-static cudaError_t setup_attr() {
-    return cudaFuncSetAttribute(persistent_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Geo<TS>::WORDS * 4);
-}
-
-int max_blocks_per_sm(int tile, int *out) {
-    cudaError_t e;
-    int n = 0;
-    if (tile == 32) {
-        if ((e = setup_attr<32>()) != cudaSuccess) return (int)e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, persistent_kernel<32>, NT, Geo<32>::WORDS * 4);
-    } else if (tile == 64) {
-        if ((e = setup_attr<64>()) != cudaSuccess) return (int)e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, persistent_kernel<64>, NT, Geo<64>::WORDS * 4);
-    } else {
-        return (int)cudaErrorInvalidValue;
+cudaError_t family_occupancy(int fam, int *n) {
+    switch (fam) {
+        case FAM_RECON_U8: return occ<FAM_RECON_U8>(n);
+        case FAM_RECON_I32: return occ<FAM_RECON_I32>(n);
+        case FAM_EDT: return occ<FAM_EDT>(n);
+        case FAM_MIXED: return occ<FAM_MIXED>(n);
+        default: return cudaErrorInvalidValue;
     }
-    *out = n;
-    return (int)e;
 }
 
 cudaError_t launch_init(const KArgs &ka, int first_attempt, cudaStream_t s) {
     int blocks = (int)((ka.tq.cap + 255) / 256);
-    if (blocks > 4096) blocks = 4096;
-    if (blocks < 1) blocks = 1;
+    blocks = blocks > 4096 ? 4096 : (blocks < 1 ? 1 : blocks);
     fill_queue_kernel<<<blocks, 256, 0, s>>>(ka, first_attempt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_persistent(const KArgs &ka, int tile, int grid, cudaStream_t s) {
-    if (tile == 32) {
-        persistent_kernel<32><<<grid, NT, Geo<32>::WORDS * 4, s>>>(ka);
-    } else if (tile == 64) {
-        persistent_kernel<64><<<grid, NT, Geo<64>::WORDS * 4, s>>>(ka);
-    } else {
-        return cudaErrorInvalidValue;
+template <int FAM>
+static void launch_fam(const KArgs &ka, int grid, cudaStream_t s) {
+    persistent_kernel<FAM><<<grid, FAM_NT[FAM], FAM_SMEM[FAM], s>>>(ka);
+}
+
+cudaError_t launch_persistent(const KArgs &ka, int fam, int grid, cudaStream_t s) {
+    switch (fam) {
+        case FAM_RECON_U8: launch_fam<FAM_RECON_U8>(ka, grid, s); break;
+        case FAM_RECON_I32: launch_fam<FAM_RECON_I32>(ka, grid, s); break;
+        case FAM_EDT: launch_fam<FAM_EDT>(ka, grid, s); break;
+        case FAM_MIXED: launch_fam<FAM_MIXED>(ka, grid, s); break;
+        default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
@@ -735,12 +1183,6 @@ cudaError_t launch_decide(const KArgs &ka, int final_step, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset(const KArgs &ka, cudaStream_t s) {
-    int blocks = (int)((ka.tq.cap + 255) / 256);
-    if (blocks > 4096) blocks = 4096;
-    if (blocks < 1) blocks = 1;
-    fill_queue_kernel<<<blocks, 256, 0, s>>>(ka, 0);
-    return cudaGetLastError();
-}
+cudaError_t launch_reset(const KArgs &ka, cudaStream_t s) { return launch_init(ka, 0, s); }
 
 }  // namespace iwpp

@@ -33,13 +33,12 @@ def run(ctx, b, fnz=False, **opts):
 
 
 @pytest.mark.parametrize("fnz", [False, True])
-@pytest.mark.parametrize("tile", [32, 64])
-def test_tiny_random_vs_bruteforce(cuda_ctx, fnz, tile):
-    rng = np.random.default_rng(500 + tile + fnz)
-    for _ in range(40):
+def test_tiny_random_vs_bruteforce(cuda_ctx, fnz):
+    rng = np.random.default_rng(500 + fnz)
+    for _ in range(80):
         h, w = (int(v) for v in rng.integers(1, 150, 2))
         b = (rng.random((h, w)) < rng.random()).astype(np.uint8)
-        sq, nn = run(cuda_ctx, b, fnz, tile=tile)
+        sq, nn = run(cuda_ctx, b, fnz)
         edt_parity(b, sq, nn, fnz, exact=oracle.edt_bruteforce(b, fnz) if h * w < 2500 else None)
 
 
@@ -88,10 +87,17 @@ def test_overflow_spill_rescan_paths(cuda_ctx):
     img, _ = synth.disks_binary(1024, 768, 4, 60, 0.3, seed=9)
     sq_o, _ = oracle.edt(img)
     ex = oracle.edt_exact(img)
-    for opts in (dict(tile=32, queue_factor=1, max_relaunch=40), dict(tile=32, spill_cap=0),
-                 dict(tile=64, spill_cap=16)):
+    for opts in (dict(queue_factor=1, max_relaunch=60), dict(spill_cap=0), dict(spill_cap=16)):
         sq, nn = run(cuda_ctx, img, **opts)
         edt_parity(img, sq, nn, sq_o=sq_o, exact=ex)
+
+
+def test_tma_and_plain_staging_agree(cuda_ctx):
+    """Width 1000 (TMA boxes, ragged last tile) and width 999 (plain loads)."""
+    for w in (1000, 999):
+        img, _ = synth.disks_binary(600, w, 4, 40, 0.3, seed=w)
+        sq, nn = run(cuda_ctx, img)
+        edt_parity(img, sq, nn)
 
 
 def test_invalid_arguments_raise(cuda_ctx):

@@ -46,9 +46,9 @@ def test_golden_small_cases(cuda_ctx):
 
 @pytest.mark.parametrize("conn", [4, 8])
 @pytest.mark.parametrize("dtype", [np.uint8, np.int32])
-@pytest.mark.parametrize("tile", [32, 64])
-def test_random_ragged(cuda_ctx, conn, dtype, tile):
-    rng = np.random.default_rng(1000 + conn + tile + (dtype == np.int32))
+@pytest.mark.parametrize("sweeps", [0, 1])
+def test_random_ragged(cuda_ctx, conn, dtype, sweeps):
+    rng = np.random.default_rng(1000 + conn + 7 * sweeps + (dtype == np.int32))
     for _ in range(12):
         h, w = (int(v) for v in rng.integers(1, 200, 2))
         if dtype == np.uint8:
@@ -57,14 +57,14 @@ def test_random_ragged(cuda_ctx, conn, dtype, tile):
         else:
             I = rng.integers(-2**31, 2**31 - 1, (h, w), dtype=np.int64).astype(np.int32)
             J = (I.astype(np.int64) - rng.integers(0, 2**31, (h, w))).clip(-2**31, 2**31 - 1).astype(np.int32)
-        np.testing.assert_array_equal(run(cuda_ctx, J, I, conn, tile=tile), oracle.fh(J, I, conn))
+        np.testing.assert_array_equal(run(cuda_ctx, J, I, conn, sweeps=sweeps), oracle.fh(J, I, conn))
 
 
 @pytest.mark.parametrize("conn", [4, 8])
-@pytest.mark.parametrize("tile", [32, 64])
-def test_config_512(cuda_ctx, conn, tile):
+@pytest.mark.parametrize("sweeps", [1, 2])
+def test_config_512(cuda_ctx, conn, sweeps):
     wl = synth.config_workload("recon512")
-    np.testing.assert_array_equal(run(cuda_ctx, wl.marker, wl.mask, conn, tile=tile),
+    np.testing.assert_array_equal(run(cuda_ctx, wl.marker, wl.mask, conn, sweeps=sweeps),
                                   oracle.fh(wl.marker, wl.mask, conn))
 
 
@@ -103,13 +103,33 @@ def test_in_place_and_pitched(cuda_ctx):
     assert (big_o[:, :50] == 7).all() and (big_o[:, 351:] == 7).all()
 
 
+@pytest.mark.parametrize("dtype", [np.uint8, np.int32])
+def test_tma_path_with_ragged_width(cuda_ctx, dtype):
+    """Row pitches that meet TMA alignment (multiple of 16 bytes) with image
+    widths that are not a multiple of the tile: boxes run past the image."""
+    marker, mask = synth.recon_inputs(700, 1000, 6.0, 50, seed=31)
+    if dtype == np.int32:
+        marker, mask = marker.astype(np.int32) * 7 - 900, mask.astype(np.int32) * 7 - 900
+    ref = oracle.fh(marker, mask, 8)
+    pitch = 1008
+    bm = torch.zeros((700, pitch), dtype=torch.from_numpy(marker).dtype, device=DEV)
+    bk = torch.zeros_like(bm)
+    bo = torch.zeros_like(bm)
+    bm[:, :1000] = gpu(marker)
+    bk[:, :1000] = gpu(mask)
+    out = cuda_ctx.recon(bm[:, :1000], bk[:, :1000], conn=8, out=bo[:, :1000])
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), ref)
+    assert (bo[:, 1000:] == 0).all()
+
+
 def test_forced_tile_queue_overflow_relaunch(cuda_ctx):
     """Section 3.2 / 5.2.4: a queue too small to hold the work drops items;
     relaunching from the partial result gives the identical output."""
     marker, mask = synth.recon_inputs(1024, 1024, 8.0, 60, seed=5)
     ref = oracle.fh(marker, mask, 8)
     cuda_ctx.stats_reset()
-    out = run(cuda_ctx, marker, mask, 8, tile=32, queue_factor=1, max_relaunch=40)
+    out = run(cuda_ctx, marker, mask, 8, queue_factor=1, max_relaunch=60)
     np.testing.assert_array_equal(out, ref)
     assert cuda_ctx.stats()["relaunches"] > 0
 
@@ -117,7 +137,7 @@ def test_forced_tile_queue_overflow_relaunch(cuda_ctx):
 def test_overflow_limit_reports_error(cuda_ctx):
     marker, mask = synth.recon_inputs(1024, 1024, 8.0, 60, seed=5)
     old = cuda_ctx.options()
-    cuda_ctx.set_options(tile=32, queue_factor=1, max_relaunch=0)
+    cuda_ctx.set_options(queue_factor=1, max_relaunch=0)
     try:
         with pytest.raises(IWPPError) as e:
             cuda_ctx.recon(gpu(marker), gpu(mask), conn=8)
@@ -135,7 +155,7 @@ def test_spill_and_rescan_paths(cuda_ctx):
     ref = oracle.fh(marker, mask, 8)
     for spill in (0, 64, 4096):
         cuda_ctx.stats_reset()
-        np.testing.assert_array_equal(run(cuda_ctx, marker, mask, 8, tile=32, sweeps=0, spill_cap=spill), ref)
+        np.testing.assert_array_equal(run(cuda_ctx, marker, mask, 8, sweeps=0, spill_cap=spill), ref)
         st = cuda_ctx.stats()
         if spill == 0:
             assert st["rescans"] > 0
