@@ -178,6 +178,34 @@ int iwpp_sync(iwpp_ctx *ctx, void *stream);
 int iwpp_stats(iwpp_ctx *ctx, iwpp_stats_t *out);
 int iwpp_stats_reset(iwpp_ctx *ctx);
 
+/*
+ * Allocation-free uint8 reconstruction (the paper has no counterpart; it
+ * exists for callers that cannot allocate device memory: code inside
+ * another allocator's accounting, real-time paths that forbid allocation
+ * after start-up, and code being recorded into a CUDA graph).
+ *
+ * Same operation and result as iwpp_recon on IWPP_U8 images, without a
+ * context: marker, mask and out are device pointers with pitches in bytes;
+ * out may be marker (in place) but not mask; conn = 4 or 8; the work is
+ * enqueued on `stream` and the call returns after it finished.  All
+ * scratch (tile queue, tile states, spill queues, status block) lives in one
+ * statically sized device array of IWPP_NOALLOC_SCRATCH_BYTES held by every
+ * GPU that loads the library until process exit; the call itself allocates
+ * nothing.  Limits and rules:
+ *   - at most IWPP_NOALLOC_MAX_TILES tiles of 64x64 pixels (e.g. 16384 x
+ *     16384); larger images return IWPP_EINVAL;
+ *   - all calls share the array: calls whose GPU work overlaps (different
+ *     streams or threads on one device) race -- serialise them;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make it before any stream capture.
+ * Returns IWPP_OK, IWPP_EINVAL, IWPP_ECUDA, IWPP_ETIMEOUT or IWPP_EOVERFLOW.
+ */
+#define IWPP_NOALLOC_MAX_TILES 65536
+#define IWPP_NOALLOC_SCRATCH_BYTES ((size_t)12 << 20)
+int iwpp_recon_u8_noalloc(const uint8_t *marker, int64_t marker_pitch, const uint8_t *mask,
+                          int64_t mask_pitch, uint8_t *out, int64_t out_pitch, int h, int w,
+                          int conn, void *stream);
+
 /* Library version as major*10000 + minor*100 + patch. */
 int iwpp_version(void);
 

@@ -77,6 +77,8 @@ SIGNATURES = {
     "iwpp_sync": (_i32, [_vp, _vp]),
     "iwpp_stats": (_i32, [_vp, ctypes.POINTER(Stats)]),
     "iwpp_stats_reset": (_i32, [_vp]),
+    "iwpp_recon_u8_noalloc": (_i32, [_vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp, ctypes.c_int64,
+                                     _i32, _i32, _i32, _vp]),
 }
 
 _lib = None
@@ -133,6 +135,26 @@ def _stream_ptr(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def recon_u8_noalloc(marker, mask, conn: int = 8, out=None, stream=None):
+    """uint8 reconstruction through the allocation-free entry point (no
+    context; library-internal static scratch).  ``out`` must be supplied by
+    callers that cannot allocate; when omitted a tensor is created here."""
+    torch = _torch()
+    lib = load_library()
+    if out is None:
+        out = torch.empty_like(mask)
+    m, k, o = image_of(marker), image_of(mask), image_of(out)
+    if not (m.dtype == k.dtype == o.dtype == IWPP_U8):
+        raise TypeError("uint8 images required")
+    if (m.h, m.w) != (k.h, k.w) or (o.h, o.w) != (k.h, k.w):
+        raise ValueError("marker, mask and out must have the same shape")
+    rc = lib.iwpp_recon_u8_noalloc(m.data, m.pitch, k.data, k.pitch, o.data, o.pitch, k.h, k.w, conn,
+                                   _stream_ptr(stream))
+    if rc != IWPP_OK:
+        raise IWPPError(rc, "iwpp_recon_u8_noalloc failed")
+    return out
 
 
 class Context:
