@@ -171,6 +171,33 @@ typedef struct {
 int iwpp_run_jobs(iwpp_ctx *ctx, int n, const iwpp_job *jobs, void *stream);
 int iwpp_run_jobs_async(iwpp_ctx *ctx, int n, const iwpp_job *jobs, void *stream);
 
+/*
+ * Plans: a fixed batch of jobs prepared once for repeated launches -- tile
+ * layout, TMA tensor maps, the device job table and the plan's own
+ * workspace are set up by iwpp_plan_create (which may allocate and copy).
+ * iwpp_plan_launch then only enqueues kernels (no allocation, no host
+ * encoding, no copies), so it is legal inside a CUDA stream capture;
+ * iwpp_plan_launch_graph captures that launch sequence into a CUDA graph
+ * on its first call and replays the graph afterwards.  The images the jobs
+ * name must stay valid while the plan lives; their contents may change
+ * between launches.  Plan launches share the context's status block: order
+ * them on one stream with the context's other calls and read failures with
+ * iwpp_sync().
+ *
+ * iwpp_plan_autotune times `reps` launches of each candidate option set
+ * (sweep sets 1..3, revisit threshold 0 / 32, blocks per SM max / max-1) on
+ * the plan's own images, keeps the fastest in the plan, stores it in the
+ * context under a key of (kernel family, log2 pixels, log2 jobs, SM count)
+ * so that later plans of the same kind start tuned, and copies it to *best
+ * (may be NULL).  It synchronises `stream`.
+ */
+typedef struct iwpp_plan iwpp_plan;
+int iwpp_plan_create(iwpp_ctx *ctx, int n, const iwpp_job *jobs, iwpp_plan **out);
+int iwpp_plan_launch(iwpp_plan *plan, void *stream);
+int iwpp_plan_launch_graph(iwpp_plan *plan, void *stream);
+int iwpp_plan_autotune(iwpp_plan *plan, void *stream, int reps, iwpp_options *best);
+int iwpp_plan_destroy(iwpp_plan *plan);
+
 /* Waits for `stream`, reads the device status of the async calls enqueued
  * on it since the last sync, returns IWPP_OK or the first failure. */
 int iwpp_sync(iwpp_ctx *ctx, void *stream);

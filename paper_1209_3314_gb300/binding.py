@@ -77,6 +77,11 @@ SIGNATURES = {
     "iwpp_sync": (_i32, [_vp, _vp]),
     "iwpp_stats": (_i32, [_vp, ctypes.POINTER(Stats)]),
     "iwpp_stats_reset": (_i32, [_vp]),
+    "iwpp_plan_create": (_i32, [_vp, _i32, ctypes.POINTER(Job), ctypes.POINTER(_vp)]),
+    "iwpp_plan_launch": (_i32, [_vp, _vp]),
+    "iwpp_plan_launch_graph": (_i32, [_vp, _vp]),
+    "iwpp_plan_autotune": (_i32, [_vp, _vp, _i32, ctypes.POINTER(Options)]),
+    "iwpp_plan_destroy": (_i32, [_vp]),
     "iwpp_recon_u8_noalloc": (_i32, [_vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp, ctypes.c_int64,
                                      _i32, _i32, _i32, _vp]),
 }
@@ -267,24 +272,68 @@ class Context:
         self._check(self.lib.iwpp_edt_batched(self.h, n, B, S, N, flags, _stream_ptr(stream)))
         return list(zip(sq, nn))
 
+    def plan(self, jobs):
+        """Prepares a fixed batch (see ``run_jobs`` for the job dicts) for
+        repeated, graph-capturable launches."""
+        return Plan(self, jobs)
+
     def run_jobs(self, jobs, stream=None, sync: bool = True):
         """Mixed batch in one launch.  ``jobs``: list of dicts, either
         {'op': 'recon', 'marker', 'mask', 'out', 'conn'} or
         {'op': 'edt', 'binary', 'sqdist', 'nearest', 'feature_nonzero'}."""
         n = len(jobs)
-        arr = (Job * n)()
-        for i, j in enumerate(jobs):
-            if j["op"] == "recon":
-                arr[i].op = IWPP_OP_RECON
-                arr[i].conn = int(j.get("conn", 8))
-                arr[i].a = image_of(j["marker"])
-                arr[i].b = image_of(j["mask"])
-                arr[i].out = image_of(j["out"])
-            else:
-                arr[i].op = IWPP_OP_EDT
-                arr[i].flags = IWPP_EDT_FEATURE_NONZERO if j.get("feature_nonzero") else 0
-                arr[i].a = image_of(j["binary"])
-                arr[i].sqdist = j["sqdist"].data_ptr()
-                arr[i].nearest = j["nearest"].data_ptr()
+        arr = _job_array(jobs)
         fn = self.lib.iwpp_run_jobs if sync else self.lib.iwpp_run_jobs_async
         self._check(fn(self.h, n, arr, _stream_ptr(stream)))
+
+
+def _job_array(jobs):
+    n = len(jobs)
+    arr = (Job * n)()
+    for i, j in enumerate(jobs):
+        if j["op"] == "recon":
+            arr[i].op = IWPP_OP_RECON
+            arr[i].conn = int(j.get("conn", 8))
+            arr[i].a = image_of(j["marker"])
+            arr[i].b = image_of(j["mask"])
+            arr[i].out = image_of(j["out"])
+        else:
+            arr[i].op = IWPP_OP_EDT
+            arr[i].flags = IWPP_EDT_FEATURE_NONZERO if j.get("feature_nonzero") else 0
+            arr[i].a = image_of(j["binary"])
+            arr[i].sqdist = j["sqdist"].data_ptr()
+            arr[i].nearest = j["nearest"].data_ptr()
+    return arr
+
+
+class Plan:
+    """A batch prepared once (C ``iwpp_plan``): launches enqueue kernels only
+    and can be replayed as a CUDA graph."""
+
+    def __init__(self, ctx: "Context", jobs):
+        self.ctx = ctx
+        self.jobs = list(jobs)  # keeps the tensors alive
+        arr = _job_array(self.jobs)
+        h = ctypes.c_void_p()
+        ctx._check(ctx.lib.iwpp_plan_create(ctx.h, len(self.jobs), arr, ctypes.byref(h)))
+        self.h = h
+
+    def launch(self, stream=None, graph: bool = False):
+        fn = self.ctx.lib.iwpp_plan_launch_graph if graph else self.ctx.lib.iwpp_plan_launch
+        self.ctx._check(fn(self.h, _stream_ptr(stream)))
+
+    def autotune(self, reps: int = 3, stream=None) -> dict:
+        o = Options()
+        self.ctx._check(self.ctx.lib.iwpp_plan_autotune(self.h, _stream_ptr(stream), reps, ctypes.byref(o)))
+        return {k: getattr(o, k) for k, _ in Options._fields_ if k != "reserved"}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.iwpp_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

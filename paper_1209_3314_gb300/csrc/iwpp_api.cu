@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -29,6 +30,7 @@ struct iwpp_ctx {
     uint64_t kernel_ns = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending_events, free_events;
     int occupancy[FAM_COUNT] = {0, 0, 0, 0};  // blocks per SM per kernel family
+    std::map<uint64_t, iwpp_options> tuned;   // autotuner results by workload key
 };
 
 namespace {
@@ -189,63 +191,99 @@ int64_t layout_jobs(std::vector<JobDesc> &jobs, int tile) {
     return base;
 }
 
-// Runs (or enqueues) the whole launch sequence for `jobs`.
-int run(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, cudaStream_t st, bool sync) {
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    const int tile = TILE;
-    const int fam = pick_family(jobs);
-    const int64_t ntiles = layout_jobs(jobs, tile);
-    for (JobDesc &j : jobs) make_maps(j);
-    if (ntiles <= 0 || ntiles > (int64_t)1 << 28) return fail(ctx, IWPP_EINVAL, "tile count %lld out of range", (long long)ntiles);
-    const int64_t cap64 = std::max<int64_t>(ntiles + 1, (int64_t)ctx->opt.queue_factor * ntiles);
-    if (cap64 > ((int64_t)1 << 31) - 1) return fail(ctx, IWPP_EINVAL, "tile queue too large");
+// A launch sequence, prepared: tile layout, TMA maps, kernel family, grid,
+// workspace layout and the kernel arguments (pointers bound to a workspace).
+struct Prepared {
+    KArgs ka;
+    int fam = 0;
+    int grid = 1;
+    int64_t ntiles = 0;
+    size_t ws_bytes = 0;
+    size_t o_slots = 0, o_state = 0, o_visited = 0, o_cnt = 0, o_spill = 0, o_jobs = 0;
+};
 
-    int &occ = ctx->occupancy[fam];
+int prepare(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, const iwpp_options &opt, Prepared &P) {
+    P.fam = pick_family(jobs);
+    P.ntiles = layout_jobs(jobs, TILE);
+    for (JobDesc &j : jobs) make_maps(j);
+    if (P.ntiles <= 0 || P.ntiles > (int64_t)1 << 28)
+        return fail(ctx, IWPP_EINVAL, "tile count %lld out of range", (long long)P.ntiles);
+    const int64_t cap64 = std::max<int64_t>(P.ntiles + 1, (int64_t)opt.queue_factor * P.ntiles);
+    if (cap64 > ((int64_t)1 << 31) - 1) return fail(ctx, IWPP_EINVAL, "tile queue too large");
+    int &occ = ctx->occupancy[P.fam];
     if (occ == 0) {
-        CK(family_occupancy(fam, &occ), "occupancy query");
+        CK(family_occupancy(P.fam, &occ), "occupancy query");
         if (occ < 1) return fail(ctx, IWPP_ECUDA, "persistent kernel does not fit on an SM");
     }
-    int bps = ctx->opt.blocks_per_sm > 0 ? std::min(ctx->opt.blocks_per_sm, occ) : occ;
-    int64_t grid64 = std::min<int64_t>(ntiles, (int64_t)bps * ctx->sm_count);
-    const int grid = (int)std::max<int64_t>(1, grid64);
-
-    // workspace layout
-    const size_t n_slots = (size_t)cap64;
+    const int bps = opt.blocks_per_sm > 0 ? std::min(opt.blocks_per_sm, occ) : occ;
+    P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(P.ntiles, (int64_t)bps * ctx->sm_count));
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-    const size_t o_slots = take(n_slots * 4);
-    const size_t o_state = take((size_t)ntiles * 4);
-    const size_t o_visited = take((size_t)ntiles * 4);
-    const size_t o_cnt = take(16);
-    const size_t o_spill = take((size_t)grid * 2 * std::max(1, ctx->opt.spill_cap) * sizeof(uint16_t));
-    const size_t o_jobs = take(jobs.size() > 1 ? jobs.size() * sizeof(JobDesc) : 0);
-    int rc = ensure_ws(ctx, off, st);
-    if (rc) return rc;
-    char *ws = (char *)ctx->ws;
-
-    KArgs ka;
+    P.o_slots = take((size_t)cap64 * 4);
+    P.o_state = take((size_t)P.ntiles * 4);
+    P.o_visited = take((size_t)P.ntiles * 4);
+    P.o_cnt = take(16);
+    P.o_spill = take((size_t)P.grid * 2 * std::max(1, opt.spill_cap) * sizeof(uint16_t));
+    P.o_jobs = take(jobs.size() > 1 ? jobs.size() * sizeof(JobDesc) : 0);
+    P.ws_bytes = off;
+    KArgs &ka = P.ka;
     memset(&ka, 0, sizeof ka);
     ka.njobs = (int)jobs.size();
-    ka.ntiles = (int)ntiles;
+    ka.ntiles = (int)P.ntiles;
     ka.job0 = jobs[0];
-    ka.jobs = jobs.size() > 1 ? (const JobDesc *)(ws + o_jobs) : nullptr;
-    ka.tq.slots = (int *)(ws + o_slots);
-    ka.tq.state = (int *)(ws + o_state);
-    ka.tq.visited = (int *)(ws + o_visited);
-    ka.tq.head = (unsigned *)(ws + o_cnt);
-    ka.tq.tail = (unsigned *)(ws + o_cnt + 4);
-    ka.tq.pending = (int *)(ws + o_cnt + 8);
     ka.tq.cap = (unsigned)cap64;
-    ka.tq.ntiles = (int)ntiles;
-    ka.ctl = ctx->ctl;
-    ka.spill = (uint16_t *)(ws + o_spill);
-    ka.spill_cap = std::max(0, ctx->opt.spill_cap);
-    ka.sweeps = ctx->opt.sweeps;
-    ka.revisit_sweep_min = ctx->opt.revisit_sweep_min;
-    ka.timeout_ns = (unsigned long long)ctx->opt.timeout_ms * 1000000ull;
+    ka.tq.ntiles = (int)P.ntiles;
+    ka.spill_cap = std::max(0, opt.spill_cap);
+    ka.sweeps = opt.sweeps;
+    ka.revisit_sweep_min = opt.revisit_sweep_min;
+    ka.timeout_ns = (unsigned long long)opt.timeout_ms * 1000000ull;
+    return IWPP_OK;
+}
 
+void bind_workspace(Prepared &P, char *ws, Control *ctl) {
+    KArgs &ka = P.ka;
+    ka.jobs = ka.njobs > 1 ? (const JobDesc *)(ws + P.o_jobs) : nullptr;
+    ka.tq.slots = (int *)(ws + P.o_slots);
+    ka.tq.state = (int *)(ws + P.o_state);
+    ka.tq.visited = (int *)(ws + P.o_visited);
+    ka.tq.head = (unsigned *)(ws + P.o_cnt);
+    ka.tq.tail = (unsigned *)(ws + P.o_cnt + 4);
+    ka.tq.pending = (int *)(ws + P.o_cnt + 8);
+    ka.ctl = ctl;
+    ka.spill = (uint16_t *)(ws + P.o_spill);
+}
+
+// Enqueues the launch sequence: queue fill, persistent kernel, then
+// `max_relaunch` device-side decide / refill / relaunch steps (no-ops when
+// nothing overflowed) and the final decide that records the outcome.
+// Kernel launches only: legal inside a stream capture.
+int enqueue(iwpp_ctx *ctx, const Prepared &P, int max_relaunch, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+    CK(launch_init(P.ka, 1, st), "launch fill_queue");
+    if (e0) CK(cudaEventRecord(e0, st), "cudaEventRecord");
+    CK(launch_persistent(P.ka, P.fam, P.grid, st), "launch persistent");
+    for (int k = 0; k < max_relaunch; ++k) {
+        CK(launch_decide(P.ka, 0, st), "launch decide");
+        CK(launch_reset(P.ka, st), "launch reset");
+        CK(launch_persistent(P.ka, P.fam, P.grid, st), "launch persistent");
+    }
+    if (e1) CK(cudaEventRecord(e1, st), "cudaEventRecord");
+    CK(launch_decide(P.ka, 1, st), "launch decide");
+    return IWPP_OK;
+}
+
+// Runs (or enqueues) the whole launch sequence for `jobs` on the context's
+// workspace.
+int run(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, cudaStream_t st, bool sync) {
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    Prepared P;
+    int rc = prepare(ctx, jobs, ctx->opt, P);
+    if (rc) return rc;
+    rc = ensure_ws(ctx, P.ws_bytes, st);
+    if (rc) return rc;
+    char *ws = (char *)ctx->ws;
+    bind_workspace(P, ws, ctx->ctl);
     if (jobs.size() > 1)
-        CK(cudaMemcpyAsync(ws + o_jobs, jobs.data(), jobs.size() * sizeof(JobDesc), cudaMemcpyHostToDevice, st),
+        CK(cudaMemcpyAsync(ws + P.o_jobs, jobs.data(), jobs.size() * sizeof(JobDesc), cudaMemcpyHostToDevice, st),
            "job table upload");
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (ctx->opt.timing) {
@@ -257,22 +295,12 @@ int run(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, cudaStream_t st, bool sync) {
             ctx->free_events.pop_back();
         }
     }
-    CK(launch_init(ka, 1, st), "launch fill_queue");
-    if (ev.first) CK(cudaEventRecord(ev.first, st), "cudaEventRecord");
-    CK(launch_persistent(ka, fam, grid, st), "launch persistent");
-    for (int k = 0; k < ctx->opt.max_relaunch; ++k) {
-        CK(launch_decide(ka, 0, st), "launch decide");
-        CK(launch_reset(ka, st), "launch reset");
-        CK(launch_persistent(ka, fam, grid, st), "launch persistent");
-    }
-    if (ev.second) {
-        CK(cudaEventRecord(ev.second, st), "cudaEventRecord");
-        ctx->pending_events.push_back(ev);
-    }
-    CK(launch_decide(ka, 1, st), "launch decide");
+    rc = enqueue(ctx, P, ctx->opt.max_relaunch, st, ev.first, ev.second);
+    if (rc) return rc;
+    if (ev.first) ctx->pending_events.push_back(ev);
     ctx->launches += 3 + 3 * (uint64_t)ctx->opt.max_relaunch;
     ctx->calls += 1;
-    ctx->tiles_initial += (uint64_t)ntiles;
+    ctx->tiles_initial += (uint64_t)P.ntiles;
     if (!sync) return IWPP_OK;
     return iwpp_sync(ctx, st);
 }
@@ -337,6 +365,76 @@ JobDesc edt_job(const iwpp_image *bin, int32_t *sq, int32_t *nn, int flags) {
     d.sqdist = sq;
     d.nearest = nn;
     return d;
+}
+
+}  // namespace
+
+
+// A prepared batch for repeated launches (see iwpp_plan_create).
+struct iwpp_plan {
+    iwpp_ctx *ctx = nullptr;
+    std::vector<iwpp_job> src;   // the jobs as given (re-prepared per option set)
+    std::vector<JobDesc> jobs;   // prepared descriptors (layout, TMA maps)
+    iwpp_options opt{};
+    Prepared P;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t cap = nullptr;  // private stream used for graph capture
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t key = 0;
+};
+
+namespace {
+
+void drop_graph(iwpp_plan *p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->exec = nullptr;
+    p->graph = nullptr;
+}
+
+// Workload key for the autotuner cache: kernel family, log2 of the pixel
+// count, log2 of the job count, SM count.
+uint64_t plan_key(const iwpp_ctx *ctx, const std::vector<JobDesc> &jobs, int fam) {
+    int64_t px = 0;
+    for (const JobDesc &j : jobs) px += (int64_t)j.h * j.w;
+    int lp = 0, lj = 0;
+    while ((1ll << lp) < px) ++lp;
+    while ((1ll << lj) < (int64_t)jobs.size()) ++lj;
+    return ((uint64_t)fam << 48) | ((uint64_t)lp << 32) | ((uint64_t)lj << 16) | (uint64_t)ctx->sm_count;
+}
+
+int jobs_from(iwpp_ctx *ctx, int n, const iwpp_job *js, std::vector<JobDesc> &jobs);
+
+// (Re)prepares the plan for option set `opt`: layout, workspace, job table.
+int plan_prepare(iwpp_plan *p, const iwpp_options &opt) {
+    iwpp_ctx *ctx = p->ctx;
+    drop_graph(p);
+    p->jobs.clear();
+    int rc = jobs_from(ctx, (int)p->src.size(), p->src.data(), p->jobs);
+    if (rc) return rc;
+    rc = prepare(ctx, p->jobs, opt, p->P);
+    if (rc) return rc;
+    if (p->P.ws_bytes > p->ws_bytes) {
+        if (p->ws) {
+            CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+            cudaFree(p->ws);
+            p->ws = nullptr;
+            p->ws_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&p->ws, p->P.ws_bytes);
+        if (e != cudaSuccess) return fail(ctx, IWPP_ENOMEM, "plan workspace: %s", cudaGetErrorString(e));
+        p->ws_bytes = p->P.ws_bytes;
+    }
+    bind_workspace(p->P, (char *)p->ws, ctx->ctl);
+    if (p->jobs.size() > 1)
+        CK(cudaMemcpy((char *)p->ws + p->P.o_jobs, p->jobs.data(), p->jobs.size() * sizeof(JobDesc),
+                      cudaMemcpyHostToDevice),
+           "job table upload");
+    p->opt = opt;
+    p->key = plan_key(ctx, p->jobs, p->P.fam);
+    return IWPP_OK;
 }
 
 }  // namespace
@@ -472,7 +570,10 @@ int iwpp_edt_batched(iwpp_ctx *ctx, int n, const iwpp_image *bins, int32_t *cons
     return run(ctx, jobs, (cudaStream_t)stream, true);
 }
 
-static int jobs_from(iwpp_ctx *ctx, int n, const iwpp_job *js, std::vector<JobDesc> &jobs) {
+}  // extern "C"
+
+namespace {
+int jobs_from(iwpp_ctx *ctx, int n, const iwpp_job *js, std::vector<JobDesc> &jobs) {
     if (n < 1 || !js) return fail(ctx, IWPP_EINVAL, "jobs: n >= 1 and an array required");
     jobs.reserve(n);
     for (int i = 0; i < n; ++i) {
@@ -490,6 +591,9 @@ static int jobs_from(iwpp_ctx *ctx, int n, const iwpp_job *js, std::vector<JobDe
     }
     return IWPP_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int iwpp_run_jobs(iwpp_ctx *ctx, int n, const iwpp_job *js, void *stream) {
     if (!ctx) return IWPP_EINVAL;
@@ -570,4 +674,134 @@ int iwpp_stats_reset(iwpp_ctx *ctx) {
     return IWPP_OK;
 }
 
+int iwpp_plan_create(iwpp_ctx *ctx, int n, const iwpp_job *jobs, iwpp_plan **out) {
+    if (!ctx || !out) return IWPP_EINVAL;
+    *out = nullptr;
+    if (n < 1 || !jobs) return fail(ctx, IWPP_EINVAL, "plan: n >= 1 and a job array required");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    iwpp_plan *p = new iwpp_plan();
+    p->ctx = ctx;
+    p->src.assign(jobs, jobs + n);
+    // a tuned option set for this kind of workload, if the autotuner ran
+    iwpp_options opt = ctx->opt;
+    {
+        std::vector<JobDesc> tmp;
+        if (jobs_from(ctx, n, jobs, tmp) == IWPP_OK) {
+            const uint64_t key = plan_key(ctx, tmp, pick_family(tmp));
+            auto it = ctx->tuned.find(key);
+            if (it != ctx->tuned.end()) opt = it->second;
+        }
+    }
+    int rc = plan_prepare(p, opt);
+    if (rc == IWPP_OK && cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess)
+        rc = fail(ctx, IWPP_ECUDA, "plan: stream creation failed");
+    if (rc) {
+        iwpp_plan_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return IWPP_OK;
+}
+
+int iwpp_plan_launch(iwpp_plan *p, void *stream) {
+    if (!p) return IWPP_EINVAL;
+    iwpp_ctx *ctx = p->ctx;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int rc = enqueue(ctx, p->P, p->opt.max_relaunch, (cudaStream_t)stream, nullptr, nullptr);
+    if (rc) return rc;
+    ctx->launches += 3 + 3 * (uint64_t)p->opt.max_relaunch;
+    ctx->calls += 1;
+    ctx->tiles_initial += (uint64_t)p->P.ntiles;
+    return IWPP_OK;
+}
+
+int iwpp_plan_launch_graph(iwpp_plan *p, void *stream) {
+    if (!p) return IWPP_EINVAL;
+    iwpp_ctx *ctx = p->ctx;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (!p->exec) {
+        CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        const int rc = enqueue(ctx, p->P, p->opt.max_relaunch, p->cap, nullptr, nullptr);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(p->cap, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+        p->graph = g;
+        CK(cudaGraphInstantiate(&p->exec, p->graph, 0), "cudaGraphInstantiate");
+    }
+    CK(cudaGraphLaunch(p->exec, (cudaStream_t)stream), "cudaGraphLaunch");
+    ctx->launches += 3 + 3 * (uint64_t)p->opt.max_relaunch;
+    ctx->calls += 1;
+    ctx->tiles_initial += (uint64_t)p->P.ntiles;
+    return IWPP_OK;
+}
+
+int iwpp_plan_autotune(iwpp_plan *p, void *stream, int reps, iwpp_options *best) {
+    if (!p || reps < 1) return IWPP_EINVAL;
+    iwpp_ctx *ctx = p->ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "cudaEventCreate");
+    CK(cudaEventCreate(&e1), "cudaEventCreate");
+    const iwpp_options base = p->opt;
+    iwpp_options best_opt = base;
+    float best_ms = 1e30f;
+    int rc = IWPP_OK;
+    const int occ = ctx->occupancy[p->P.fam];
+    const int sweeps_c[3] = {1, 2, 3};
+    const int revisit_c[2] = {0, 32};
+    const int bps_c[2] = {0, occ > 2 ? occ - 1 : 0};
+    for (int a = 0; a < 3 && rc == IWPP_OK; ++a)
+        for (int b = 0; b < 2 && rc == IWPP_OK; ++b)
+            for (int c = 0; c < 2 && rc == IWPP_OK; ++c) {
+                if (c == 1 && bps_c[1] == 0) continue;
+                iwpp_options o = base;
+                o.sweeps = sweeps_c[a];
+                o.revisit_sweep_min = revisit_c[b];
+                o.blocks_per_sm = bps_c[c];
+                if ((rc = plan_prepare(p, o))) break;
+                if ((rc = iwpp_plan_launch(p, st))) break;  // warm-up
+                if ((rc = iwpp_sync(ctx, st))) break;
+                CK(cudaEventRecord(e0, st), "cudaEventRecord");
+                for (int r = 0; r < reps && rc == IWPP_OK; ++r) rc = iwpp_plan_launch(p, st);
+                CK(cudaEventRecord(e1, st), "cudaEventRecord");
+                if (rc || (rc = iwpp_sync(ctx, st))) break;
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_opt = o;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        plan_prepare(p, base);
+        return rc;
+    }
+    rc = plan_prepare(p, best_opt);
+    if (rc) return rc;
+    ctx->tuned[p->key] = best_opt;
+    if (best) *best = best_opt;
+    return IWPP_OK;
+}
+
+int iwpp_plan_destroy(iwpp_plan *p) {
+    if (!p) return IWPP_OK;
+    cudaSetDevice(p->ctx->device);
+    drop_graph(p);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(p->ws);
+    }
+    delete p;
+    return IWPP_OK;
+}
+
 }  // extern "C"
+
