@@ -198,6 +198,46 @@ int iwpp_plan_launch_graph(iwpp_plan *plan, void *stream);
 int iwpp_plan_autotune(iwpp_plan *plan, void *stream, int reps, iwpp_options *best);
 int iwpp_plan_destroy(iwpp_plan *plan);
 
+/*
+ * Served mode: a continuous-batching request server on one GPU.  Requests
+ * name HOST images (dense, row-major; pinned memory gives overlapped
+ * copies).  A worker thread admits queued requests while their device
+ * memory fits `hbm_budget_bytes` next to the work in flight, runs each
+ * admitted group as one persistent launch on one of `streams` streams
+ * (each with its own resident context), and keeps admitting new arrivals
+ * onto free streams while earlier batches run.  Results are copied back to
+ * the request's host buffers; the latency reported is submit-to-completion.
+ * A request larger than the whole budget completes with IWPP_ENOMEM.
+ * iwpp_server_destroy finishes every submitted request first.
+ */
+typedef struct {
+    int32_t op;             /* IWPP_OP_RECON or IWPP_OP_EDT                      */
+    int32_t conn;           /* reconstruction: 4 or 8                            */
+    int32_t flags;          /* distance transform: IWPP_EDT_FEATURE_*            */
+    int32_t dtype;          /* reconstruction: IWPP_U8 or IWPP_I32               */
+    int32_t h, w;
+    const void *marker;     /* recon: marker; edt: binary image (uint8)          */
+    const void *mask;       /* recon: mask                                       */
+    void *out;              /* recon: result                                     */
+    int32_t *sqdist;        /* edt: squared distances (h*w)                      */
+    int32_t *nearest;       /* edt: nearest-feature linear indices (h*w)         */
+} iwpp_request;
+
+typedef struct {
+    uint64_t submitted, completed, batches, pending;
+    uint64_t bytes_in_use, peak_bytes_in_use;
+} iwpp_server_stats_t;
+
+typedef struct iwpp_server iwpp_server;
+int iwpp_server_create(iwpp_server **out, int device, size_t hbm_budget_bytes, int streams, int max_batch);
+int iwpp_server_submit(iwpp_server *srv, const iwpp_request *req, uint64_t *ticket);
+/* 1 when the request finished (its status in *status), 0 while pending. */
+int iwpp_server_poll(iwpp_server *srv, uint64_t ticket, int *status);
+/* Blocks until the request finished; *status is its outcome. */
+int iwpp_server_wait(iwpp_server *srv, uint64_t ticket, int *status, double *latency_ms);
+int iwpp_server_stats(iwpp_server *srv, iwpp_server_stats_t *out);
+int iwpp_server_destroy(iwpp_server *srv);
+
 /* Waits for `stream`, reads the device status of the async calls enqueued
  * on it since the last sync, returns IWPP_OK or the first failure. */
 int iwpp_sync(iwpp_ctx *ctx, void *stream);

@@ -49,6 +49,18 @@ class Options(ctypes.Structure):
                 ("revisit_sweep_min", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("conn", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("h", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("marker", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("sqdist", ctypes.c_void_p), ("nearest", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "batches", "pending",
+                                                 "bytes_in_use", "peak_bytes_in_use")]
+
+
 class Job(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int32), ("conn", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("a", Image), ("b", Image), ("out", Image),
@@ -82,6 +94,12 @@ SIGNATURES = {
     "iwpp_plan_launch_graph": (_i32, [_vp, _vp]),
     "iwpp_plan_autotune": (_i32, [_vp, _vp, _i32, ctypes.POINTER(Options)]),
     "iwpp_plan_destroy": (_i32, [_vp]),
+    "iwpp_server_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.c_size_t, _i32, _i32]),
+    "iwpp_server_submit": (_i32, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "iwpp_server_poll": (_i32, [_vp, ctypes.c_uint64, ctypes.POINTER(_i32)]),
+    "iwpp_server_wait": (_i32, [_vp, ctypes.c_uint64, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]),
+    "iwpp_server_stats": (_i32, [_vp, ctypes.POINTER(ServerStats)]),
+    "iwpp_server_destroy": (_i32, [_vp]),
     "iwpp_recon_u8_noalloc": (_i32, [_vp, ctypes.c_int64, _vp, ctypes.c_int64, _vp, ctypes.c_int64,
                                      _i32, _i32, _i32, _vp]),
 }
@@ -331,6 +349,77 @@ class Plan:
         if getattr(self, "h", None):
             self.ctx.lib.iwpp_plan_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (C ``iwpp_server``).  Requests
+    carry host (CPU) tensors, ideally pinned; results land in the request's
+    output tensors.  The tensors must stay alive until the request is done."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 120 << 30, streams: int = 3, max_batch: int = 64):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        rc = self.lib.iwpp_server_create(ctypes.byref(h), device, hbm_budget, streams, max_batch)
+        if rc != IWPP_OK:
+            raise IWPPError(rc, "iwpp_server_create failed")
+        self.h = h
+        self._keep = {}
+
+    def submit_recon(self, marker, mask, out, conn: int = 8) -> int:
+        import numpy as np  # noqa: F401
+
+        r = Request()
+        r.op, r.conn = IWPP_OP_RECON, conn
+        r.dtype = IWPP_U8 if marker.dtype.itemsize == 1 else IWPP_I32
+        r.h, r.w = marker.shape
+        r.marker, r.mask, r.out = marker.data_ptr(), mask.data_ptr(), out.data_ptr()
+        return self._submit(r, (marker, mask, out))
+
+    def submit_edt(self, binary, sqdist, nearest, feature_nonzero: bool = False) -> int:
+        r = Request()
+        r.op = IWPP_OP_EDT
+        r.flags = IWPP_EDT_FEATURE_NONZERO if feature_nonzero else 0
+        r.h, r.w = binary.shape
+        r.marker, r.sqdist, r.nearest = binary.data_ptr(), sqdist.data_ptr(), nearest.data_ptr()
+        return self._submit(r, (binary, sqdist, nearest))
+
+    def _submit(self, r, keep):
+        for t in keep:
+            if t.device.type != "cpu" or not t.is_contiguous():
+                raise ValueError("server requests take contiguous host tensors")
+        t = ctypes.c_uint64()
+        rc = self.lib.iwpp_server_submit(self.h, ctypes.byref(r), ctypes.byref(t))
+        if rc != IWPP_OK:
+            raise IWPPError(rc, "iwpp_server_submit failed")
+        self._keep[t.value] = keep
+        return t.value
+
+    def wait(self, ticket: int):
+        """Returns (status, latency_ms)."""
+        st = ctypes.c_int()
+        lat = ctypes.c_double()
+        rc = self.lib.iwpp_server_wait(self.h, ticket, ctypes.byref(st), ctypes.byref(lat))
+        if rc != IWPP_OK:
+            raise IWPPError(rc, "iwpp_server_wait failed")
+        self._keep.pop(ticket, None)
+        return st.value, lat.value
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        self.lib.iwpp_server_stats(self.h, ctypes.byref(s))
+        return {k: int(getattr(s, k)) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.iwpp_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
 
     def __del__(self):
         try:
