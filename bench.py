@@ -208,6 +208,155 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def bench_batched(ctx, dev, n, reps):
+    """512 mixed images (sides log-uniform 256..2048, half reconstruction,
+    half EDT) in ONE persistent launch from an autotuned plan replayed as a
+    CUDA graph, against one launch per image on the same GPU."""
+    import torch
+
+    from paper_1209_3314_gb300 import synth
+
+    wls = synth.batched_from_pool(n, seed=3000)
+    jobs, px = [], 0
+    for wl in wls:
+        px += wl.pixels
+        if wl.op == "recon":
+            wp = (wl.w + 15) // 16 * 16  # TMA-aligned pitch
+            buf = torch.zeros((3, wl.h, wp), dtype=torch.uint8, device=dev)
+            buf[0, :, :wl.w] = torch.from_numpy(wl.marker).to(dev)
+            buf[1, :, :wl.w] = torch.from_numpy(wl.mask).to(dev)
+            jobs.append({"op": "recon", "marker": buf[0, :, :wl.w], "mask": buf[1, :, :wl.w],
+                         "out": buf[2, :, :wl.w], "conn": 8})
+        else:
+            b = torch.from_numpy(wl.binary).to(dev)
+            jobs.append({"op": "edt", "binary": b,
+                         "sqdist": torch.empty(b.shape, dtype=torch.int32, device=dev),
+                         "nearest": torch.empty(b.shape, dtype=torch.int32, device=dev)})
+    plan = ctx.plan(jobs)
+    tuned = plan.autotune(reps=2)
+    plan.launch(graph=True)
+    ctx.sync()
+    st = torch.cuda.current_stream(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        plan.launch(graph=True)
+    b.record(st)
+    ctx.sync()
+    ms = a.elapsed_time(b) / reps
+
+    def one_per_launch():
+        for j in jobs:
+            if j["op"] == "recon":
+                ctx.recon(j["marker"], j["mask"], 8, out=j["out"], sync=False)
+            else:
+                ctx.edt(j["binary"], sqdist=j["sqdist"], nearest=j["nearest"], sync=False)
+
+    one_per_launch()
+    ctx.sync()
+    a.record(st)
+    one_per_launch()
+    b.record(st)
+    ctx.sync()
+    base_ms = a.elapsed_time(b)
+    plan.close()
+    return {"images": n, "pixels": px, "ms_per_batch": round(ms, 3), "imgs_s": round(n / ms * 1e3, 1),
+            "mpx_s": round(px / ms / 1e3, 1), "one_per_launch_ms": round(base_ms, 3),
+            "one_per_launch_imgs_s": round(n / base_ms * 1e3, 1), "speedup": round(base_ms / ms, 2),
+            "launch": "one persistent launch per batch, CUDA graph replay, autotuned",
+            "tuned": {k: tuned[k] for k in ("sweeps", "revisit_sweep_min", "blocks_per_sm")}}
+
+
+def bench_served(ctx, dev, rates, duration, budget):
+    """Poisson arrivals of mixed reconstruction / EDT requests, square sides
+    log-uniform 512..8192 (host images, pinned), served by the
+    continuous-batching server under an HBM budget, against one job per
+    launch in arrival order."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_1209_3314_gb300 import synth
+    from paper_1209_3314_gb300.binding import Server
+
+    marker8k, mask8k, bin8k = synth.served_pool(8192, seed=4000)
+    rng = np.random.default_rng(4100)
+    templates = []
+    for k in range(24):
+        side = int(round(math.exp(rng.uniform(math.log(512), math.log(8192)))))
+        y, x = (int(v) for v in rng.integers(0, 8192 - side + 1, 2))
+        if k % 2 == 0:
+            templates.append({"op": "recon", "px": side * side,
+                              "marker": torch.from_numpy(np.ascontiguousarray(marker8k[y:y + side, x:x + side])).pin_memory(),
+                              "mask": torch.from_numpy(np.ascontiguousarray(mask8k[y:y + side, x:x + side])).pin_memory(),
+                              "out": torch.empty((side, side), dtype=torch.uint8).pin_memory()})
+        else:
+            templates.append({"op": "edt", "px": side * side,
+                              "binary": torch.from_numpy(np.ascontiguousarray(bin8k[y:y + side, x:x + side])).pin_memory(),
+                              "sqdist": torch.empty((side, side), dtype=torch.int32).pin_memory(),
+                              "nearest": torch.empty((side, side), dtype=torch.int32).pin_memory()})
+    results = {}
+    for rate in rates:
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * duration) + 1))
+        arr = arr[arr < duration]
+        seq = [templates[i % len(templates)] for i in range(len(arr))]
+        px = sum(t["px"] for t in seq)
+        # continuous-batching server
+        srv = Server(0, hbm_budget=budget, streams=3, max_batch=32)
+        t0 = time.perf_counter()
+        tickets = []
+        for when, t in zip(arr, seq):
+            while time.perf_counter() - t0 < when:
+                pass
+            if t["op"] == "recon":
+                tickets.append(srv.submit_recon(t["marker"], t["mask"], t["out"]))
+            else:
+                tickets.append(srv.submit_edt(t["binary"], t["sqdist"], t["nearest"]))
+        lat = [srv.wait(tk)[1] for tk in tickets]
+        span = time.perf_counter() - t0
+        srv.close()
+        # one job per launch, in arrival order
+        d_in = torch.empty(3 * 8192 * 8192, dtype=torch.uint8, device=dev)
+        d_sq = torch.empty(8192 * 8192, dtype=torch.int32, device=dev)
+        d_nn = torch.empty(8192 * 8192, dtype=torch.int32, device=dev)
+        base_lat = []
+        t0 = time.perf_counter()
+        for when, t in zip(arr, seq):
+            while time.perf_counter() - t0 < when:
+                pass
+            if t["op"] == "recon":
+                h, w = t["mask"].shape
+                m = d_in[:h * w].view(h, w)
+                k = d_in[h * w:2 * h * w].view(h, w)
+                o = d_in[2 * h * w:3 * h * w].view(h, w)
+                m.copy_(t["marker"], non_blocking=True)
+                k.copy_(t["mask"], non_blocking=True)
+                ctx.recon(m, k, 8, out=o)
+                t["out"].copy_(o)
+            else:
+                h, w = t["binary"].shape
+                bb = d_in[:h * w].view(h, w)
+                bb.copy_(t["binary"], non_blocking=True)
+                sq, nn = d_sq[:h * w].view(h, w), d_nn[:h * w].view(h, w)
+                ctx.edt(bb, sqdist=sq, nearest=nn)
+                t["sqdist"].copy_(sq)
+                t["nearest"].copy_(nn)
+            base_lat.append((time.perf_counter() - t0 - when) * 1e3)
+        base_span = time.perf_counter() - t0
+        del d_in, d_sq, d_nn
+        results[str(rate)] = {
+            "requests": len(seq), "mpx": round(px / 1e6, 1),
+            "served": {"req_s": round(len(seq) / span, 1), "mpx_s": round(px / span / 1e6, 1),
+                       "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                       "p99_ms": round(float(np.percentile(lat, 99)), 3)},
+            "one_per_launch": {"req_s": round(len(seq) / base_span, 1), "mpx_s": round(px / base_span / 1e6, 1),
+                               "p50_ms": round(float(np.percentile(base_lat, 50)), 3),
+                               "p99_ms": round(float(np.percentile(base_lat, 99)), 3)}}
+    return {"duration_s": duration, "hbm_budget_gb": round(budget / 2**30, 1),
+            "sizes": "square sides log-uniform 512..8192, alternating recon / EDT", "rates": results}
+
+
 def run_gpu(args, ws, rank, local):
     import numpy as np
     import torch
@@ -324,6 +473,13 @@ def run_gpu(args, ws, rank, local):
                "sample": f"top-left {s}x{s} crop of both images, Algorithm 2 ({tr:.1f} s) + "
                          f"Algorithm 3 ({te:.1f} s), one thread"}
 
+    batched = served = None
+    if rank == 0 and not args.skip_batched:
+        batched = bench_batched(ctx, dev, args.batch_images, max(1, args.steps // 2))
+    if rank == 0 and not args.skip_served:
+        rates = [int(r) for r in args.serve_rates.split(",") if r]
+        served = bench_served(ctx, dev, rates, args.serve_duration, 120 << 30)
+
     traffic = profiled_traffic(f"persistent_{dominant}", side)
     if rank == 0:
         line = {
@@ -346,6 +502,8 @@ def run_gpu(args, ws, rank, local):
                          "kernel_ms_mean_per_call": round(kern_ms, 4)},
             "queue": {k: st[k] for k in ("tiles_processed", "tiles_initial", "seeds", "pushes",
                                          "spills", "rescans", "relaunches", "rounds")},
+            "batched": batched,
+            "served": served,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_val, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3), "check": ok},
@@ -367,6 +525,11 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=8192)
     ap.add_argument("--reference-sample", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-served", action="store_true")
+    ap.add_argument("--batch-images", type=int, default=512)
+    ap.add_argument("--serve-rates", default="200,500,1000,2000")
+    ap.add_argument("--serve-duration", type=float, default=1.0)
     args = ap.parse_args()
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:

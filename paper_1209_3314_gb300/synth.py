@@ -205,6 +205,40 @@ def batched_workloads(n: int = 512, seed: int = 3000, smin: int = 256,
     return out
 
 
+def _crop(rng, img, h, w):
+    H, W = img.shape
+    y = int(rng.integers(0, H - h + 1))
+    x = int(rng.integers(0, W - w + 1))
+    return np.ascontiguousarray(img[y:y + h, x:x + w])
+
+
+def batched_from_pool(n: int = 512, seed: int = 3000, smin: int = 256, smax: int = 2048,
+                      pool_side: int = 2048) -> list[Workload]:
+    """The batched mix, built fast from a small pool: half reconstruction
+    (random crops of blurred-noise masks with sigma 2, 4, 6, 8, marker =
+    mask - offset, offset ~ U{20..80}) and half EDT (random crops of disk
+    images, r in [4, 40], at 10, 20, 30 and 40 % foreground).  Sides are
+    log-uniform in [smin, smax], independently for h and w."""
+    rng = np.random.default_rng(seed)
+    masks = [blurred_noise_u8(pool_side, pool_side, s, seed + k) for k, s in enumerate((2.0, 4.0, 6.0, 8.0))]
+    disks = [disks_binary(pool_side, pool_side, 4, 40, c, seed + 10 + k)[0]
+             for k, c in enumerate((0.10, 0.20, 0.30, 0.40))]
+    out = []
+    for i in range(n):
+        h = int(round(math.exp(rng.uniform(math.log(smin), math.log(smax)))))
+        w = int(round(math.exp(rng.uniform(math.log(smin), math.log(smax)))))
+        h, w = min(h, pool_side), min(w, pool_side)
+        k = int(rng.integers(0, 4))
+        if i % 2 == 0:
+            mask = _crop(rng, masks[k], h, w)
+            off = int(rng.integers(20, 81))
+            marker = np.maximum(mask.astype(np.int16) - off, 0).astype(np.uint8)
+            out.append(Workload("recon", h, w, marker=marker, mask=mask, note=f"pool{k} off={off}"))
+        else:
+            out.append(Workload("edt", h, w, binary=_crop(rng, disks[k], h, w), note=f"disks{k}"))
+    return out
+
+
 def served_pool(side: int = 8192, seed: int = 4000):
     """Source images for served jobs: one large recon pair and one binary image;
     a job of side s is a random s x s crop of them (crops of blurred noise and
