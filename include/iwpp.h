@@ -74,6 +74,8 @@ typedef struct {
     uint64_t rounds;           /* propagation rounds summed over tile visits     */
     uint64_t wait_ns;          /* time persistent CTAs spent waiting for a tile, summed */
     uint64_t visit_ns;         /* time persistent CTAs spent visiting tiles, summed     */
+    uint64_t phase_ns[4];      /* visit time by phase: staging, sweeps and seeds,
+                                  queue rounds, store and border test (summed)  */
     uint64_t kernel_launches;  /* kernels this library launched                  */
     uint64_t kernel_ns;        /* device time from the first to the last persistent
                                   launch of each call, summed (only while the

@@ -36,9 +36,11 @@ class Image(ctypes.Structure):
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_uint64) for n in (
+    _fields_ = ([(n, ctypes.c_uint64) for n in (
         "calls", "tiles_processed", "tiles_initial", "seeds", "pushes", "spills",
-        "rescans", "relaunches", "rounds", "wait_ns", "visit_ns", "kernel_launches", "kernel_ns")]
+        "rescans", "relaunches", "rounds", "wait_ns", "visit_ns")] +
+        [("phase_ns", ctypes.c_uint64 * 4)] +
+        [(n, ctypes.c_uint64) for n in ("kernel_launches", "kernel_ns")])
 
 
 class Options(ctypes.Structure):
@@ -225,7 +227,9 @@ class Context:
     def stats(self) -> dict:
         s = Stats()
         self._check(self.lib.iwpp_stats(self.h, ctypes.byref(s)))
-        return {k: int(getattr(s, k)) for k, _ in Stats._fields_}
+        d = {k: getattr(s, k) for k, _ in Stats._fields_}
+        d["phase_ns"] = [int(v) for v in s.phase_ns]
+        return {k: (v if isinstance(v, list) else int(v)) for k, v in d.items()}
 
     def stats_reset(self):
         self._check(self.lib.iwpp_stats_reset(self.h))

@@ -653,6 +653,7 @@ int iwpp_stats(iwpp_ctx *ctx, iwpp_stats_t *out) {
     out->rounds = c.rounds;
     out->wait_ns = c.wait_ns;
     out->visit_ns = c.visit_ns;
+    for (int i = 0; i < 4; ++i) out->phase_ns[i] = c.phase_ns[i];
     out->kernel_launches = ctx->launches;
     out->kernel_ns = ctx->kernel_ns;
     return IWPP_OK;
@@ -666,6 +667,7 @@ int iwpp_stats_reset(iwpp_ctx *ctx) {
     CK(cudaMemcpy(&c, ctx->ctl, sizeof c, cudaMemcpyDeviceToHost), "stats readback");
     c.tiles_processed = c.seeds = c.pushes = c.spills = c.rescans = c.relaunches = c.rounds = 0;
     c.wait_ns = c.visit_ns = 0;
+    for (int i = 0; i < 4; ++i) c.phase_ns[i] = 0;
     CK(cudaMemcpy(ctx->ctl, &c, sizeof c, cudaMemcpyHostToDevice), "stats reset");
     ctx->calls = 0;
     ctx->tiles_initial = 0;

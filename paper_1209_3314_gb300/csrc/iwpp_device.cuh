@@ -42,6 +42,7 @@ struct Control {
     unsigned long long rounds;
     unsigned long long wait_ns;   // summed time CTAs waited for a tile
     unsigned long long visit_ns;  // summed time CTAs spent visiting tiles
+    unsigned long long phase_ns[4];  // visit phases: stage, sweep+seed, queue, store+border
 };
 
 // Tile queue: a linear array of `cap` slots filled once each.  Tickets

@@ -66,12 +66,13 @@ enum : int {
     H_FLAG = 13,  // 3x3 neighbourhood: needs a visit
     H_PUSH = 22, H_SPILL = 23, H_RESC = 24, H_SEEDS = 25, H_ROUNDS = 26,
     H_OFF = 32,   // 9 neighbour offsets of the current layout
+    H_PH = 48,    // 4 phase durations of the visit (ns, low 32 bits)
 };
 constexpr int HDR_BYTES = 512;  // header ints + mbarrier at byte 256
 
 // byte offsets of the layouts
 constexpr int RU8_JW = HDR_BYTES, RU8_IW = RU8_JW + WU8_PAD, RU8_U = RU8_IW + WU8_PAD;
-constexpr int RU8_BYTES = RU8_U + 3 * BU8_PAD;
+constexpr int RU8_BYTES = RU8_U + 2 * BU8_PAD;
 constexpr int RI32_J = HDR_BYTES, RI32_I = RI32_J + BI32_PAD, RI32_U = RI32_I + BI32_PAD;
 constexpr int RI32_BYTES = RI32_U + BI32_PAD;
 constexpr int E_W = HDR_BYTES, E_U = E_W + WE_PAD;
@@ -79,7 +80,7 @@ constexpr int E_BYTES = E_U + BU8_PAD + BI32_PAD;
 static_assert(RU8_U % 128 == 0 && RI32_J % 128 == 0 && RI32_I % 128 == 0 && RI32_U % 128 == 0 &&
                   E_U % 128 == 0 && (E_U + BU8_PAD) % 128 == 0,
               "TMA destinations must be 128-byte aligned");
-static_assert(2 * QCAP_R * 2 <= 3 * BU8_PAD && 2 * QCAP_R * 2 <= BI32_PAD &&
+static_assert(2 * QCAP_R * 2 <= 2 * BU8_PAD && 2 * QCAP_R * 2 <= BI32_PAD &&
                   2 * QCAP_E * 2 <= BU8_PAD + BI32_PAD,
               "queues must fit the staging union");
 static_assert(RR * WE_P * 8 <= WE_PAD, "EDT working array");
@@ -136,21 +137,44 @@ __device__ __forceinline__ void begin_visit(int *hdr) {
     if (tid == 0) {
         hdr[H_CNT0] = 0; hdr[H_CNT1] = 0; hdr[H_RESCAN] = 0;
         hdr[H_PUSH] = 0; hdr[H_SPILL] = 0; hdr[H_RESC] = 0; hdr[H_SEEDS] = 0; hdr[H_ROUNDS] = 0;
+        hdr[H_PH] = hdr[H_PH + 1] = hdr[H_PH + 2] = hdr[H_PH + 3] = 0;
     }
 }
 
-// Publishes the tile's stores, queues flagged neighbours, marks the tile
-// visited and ends the visit.  Thread 0; all stores precede it (barrier).
-__device__ __forceinline__ void finish_tile(const KArgs &ka, const JobDesc *jd, int gt, int tx, int ty, int *hdr) {
-    __threadfence();
-    if (hdr[H_SRC + 4] != 1) st_release(ka.tq.visited + gt, 1);
-    for (int k = 0; k < 9; ++k) {
-        if (k == 4 || !hdr[H_FLAG + k]) continue;
-        const int ny = ty + k / 3 - 1, nx = tx + k % 3 - 1;
-        tq_push(ka.tq, ka.ctl, jd->tile_base + ny * jd->tiles_x + nx);
+// Marks the tile visited once its result is stored (thread 0; the barrier
+// before it completed every thread's stores).
+__device__ __forceinline__ void publish_tile(const KArgs &ka, int gt, int *hdr) {
+    if (threadIdx.x == 0 && hdr[H_SRC + 4] != 1) {
+        __threadfence();
+        st_release(ka.tq.visited + gt, 1);
     }
-    tq_finish(ka.tq, ka.ctl, gt);
 }
+
+// Queues the flagged neighbours (threads 0..8, one neighbour each, in
+// parallel) and ends the visit.  Called by all threads after the border
+// test; the pushes precede the caller's pending-count decrement.
+__device__ __forceinline__ void finish_tile(const KArgs &ka, const JobDesc *jd, int gt, int tx, int ty, int *hdr) {
+    const int k = threadIdx.x;
+    if (k < 9 && k != 4 && hdr[H_FLAG + k]) {
+        __threadfence();
+        tq_push(ka.tq, ka.ctl, jd->tile_base + (ty + k / 3 - 1) * jd->tiles_x + tx + k % 3 - 1);
+    }
+    __syncthreads();
+    if (k == 0) tq_finish(ka.tq, ka.ctl, gt);
+}
+
+// Per-visit phase timing (thread 0): mark(i) closes phase i.
+struct PhaseClock {
+    unsigned long long t;
+    __device__ __forceinline__ void start() { if (threadIdx.x == 0) t = globaltimer_ns(); }
+    __device__ __forceinline__ void mark(int *hdr, int i) {
+        if (threadIdx.x == 0) {
+            const unsigned long long n = globaltimer_ns();
+            hdr[H_PH + i] += (int)(n - t);
+            t = n;
+        }
+    }
+};
 
 // neighbour offsets in a layout with row pitch P -> hdr[H_OFF..]; entry 8
 // is 0 (the pixel itself)
@@ -298,7 +322,7 @@ __device__ __forceinline__ bool wait_boxes(uint64_t *bar, uint32_t &phase, unsig
 // Row passes (N^{+,0} left to right, then N^{-,0} right to left) of one
 // uint8 working row; one thread owns the row during the pass, so plain
 // loads can run ahead of the running value.
-__device__ __forceinline__ bool u8_row_passes(uint8_t *J, const uint8_t *I, int r) {
+__device__ __forceinline__ bool u8_row_passes(uint8_t *__restrict__ J, const uint8_t *__restrict__ I, int r) {
     const int base = r * WU8_P + 3;
     bool ch = false;
     int run = J[base];
@@ -321,7 +345,7 @@ __device__ __forceinline__ bool u8_row_passes(uint8_t *J, const uint8_t *I, int 
 }
 
 // Row passes for int32 rows (one thread per row).
-__device__ __forceinline__ bool i32_row_passes(int *J, const int *I, int base) {
+__device__ __forceinline__ bool i32_row_passes(int *__restrict__ J, const int *__restrict__ I, int base) {
     bool ch = false;
     int run = J[base];
     for (int c = 1; c <= TS; ++c) {
@@ -347,7 +371,7 @@ __device__ __forceinline__ bool i32_row_passes(int *J, const int *I, int base) {
 // where another warp may not have written it yet -- an older value, which
 // is still a valid lower bound.
 template <int CONN, int DIR, typename T>
-__device__ __forceinline__ bool column_pass(T *J, const T *I, int P, int c0) {
+__device__ __forceinline__ bool column_pass(T *__restrict__ J, const T *__restrict__ I, int P, int c0) {
     const int lane = threadIdx.x & 31;
     const int c = threadIdx.x + 1;
     const int r0 = DIR > 0 ? 0 : RR - 1;
@@ -418,7 +442,7 @@ __device__ bool sweep_set_i32(int *J, const int *I) {
 // One thread per column slides a 3-row window down the tile; each pixel is
 // written only by its own thread.
 template <int CONN, int NT, typename T>
-__device__ unsigned dilate_seed(T *J, const T *I, int P, int c0, const RQ &q, const int *off) {
+__device__ unsigned dilate_seed(T *__restrict__ J, const T *__restrict__ I, int P, int c0, const RQ &q, const int *off) {
     unsigned pushed = 0;
     const int t = threadIdx.x;
     if (t >= ((TS + 31) / 32) * 32) return 0;  // whole warps only
@@ -532,7 +556,7 @@ __device__ unsigned halo_seed(const G &g, const RQ &q, const int *off) {
 
 template <int CONN, int NT, typename G>
 __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t *Q0, uint16_t *Q1, bool first,
-                                const int *off) {
+                                const int *off, PhaseClock &pc) {
     uint16_t *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
     RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, QCAP_R, ka.spill_cap};
     auto sweeps_then_dilate = [&](const RQ &q) -> unsigned {
@@ -559,6 +583,7 @@ __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t 
         }
     }
     if ((threadIdx.x & 31) == 0) atomicAdd(hdr + H_SEEDS, (int)seeds);
+    pc.mark(hdr, 1);
     auto proc = [&](int p) -> unsigned {
         const int jp = g.j(p);
         const int pr = p / G::P, pc = p - pr * G::P - 3;
@@ -575,6 +600,7 @@ __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t 
     };
     auto rescan = [&](const RQ &q) -> unsigned { return g.template dilate<CONN, NT>(q, off); };
     run_rounds<NT>(hdr, Q0, Q1, QCAP_R, spill, ka.spill_cap, off, proc, rescan);
+    pc.mark(hdr, 2);
 }
 
 // Border test against the neighbours' current values; flags hdr[H_FLAG..].
@@ -611,8 +637,7 @@ __device__ bool recon_u8_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
     uint8_t *JW = (uint8_t *)(sm + RU8_JW);
     uint8_t *IW = (uint8_t *)(sm + RU8_IW);
     uint8_t *IB = (uint8_t *)(sm + RU8_U);
-    uint8_t *JBm = IB + BU8_PAD;      // marker box
-    uint8_t *JBo = IB + 2 * BU8_PAD;  // current-result box
+    uint8_t *JB = IB + BU8_PAD;  // the tile's own J source (marker or current result)
     uint16_t *Q0 = (uint16_t *)(sm + RU8_U), *Q1 = Q0 + QCAP_R;
     const int tid = threadIdx.x;
     const int lt = gt - jd->tile_base, tx = lt % jd->tiles_x, ty = lt / jd->tiles_x;
@@ -620,61 +645,58 @@ __device__ bool recon_u8_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
     const uint8_t *mk = (const uint8_t *)jd->a, *ms = (const uint8_t *)jd->b;
     uint8_t *out = (uint8_t *)jd->out;
 
+    PhaseClock pc;
+    pc.start();
     load_sources(ka, jd, tx, ty, hdr);
     begin_visit(hdr);
     make_offsets<CONN, WU8_P>(hdr);
     __syncthreads();
-    int need_m = 0, need_o = 0;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        need_m |= hdr[H_SRC + k] == 0;
-        need_o |= hdr[H_SRC + k] == 1;
-    }
     const bool first = hdr[H_SRC + 4] == 0;
+    const uint8_t *jsrc = first ? mk : out;
+    const int64_t jpitch = first ? jd->pa : jd->po;
 
-    // 1. stage the mask, marker and/or current-result boxes
+    // 1. stage the mask box and the box of the tile's own J source
     if (jd->use_tma) {
         if (tid == 0) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, BU8_BYTES * (1 + need_m + need_o));
+            mbar_arrive_expect_tx(bar, 2 * BU8_BYTES);
             tma_load_2d(IB, &jd->tm[1], x0 - 16, y0 - 1, bar);
-            if (need_m) tma_load_2d(JBm, &jd->tm[0], x0 - 16, y0 - 1, bar);
-            if (need_o) tma_load_2d(JBo, &jd->tm[2], x0 - 16, y0 - 1, bar);
+            tma_load_2d(JB, &jd->tm[first ? 0 : 2], x0 - 16, y0 - 1, bar);
         }
         if (!wait_boxes(bar, phase, deadline, ka.ctl)) return false;
     } else {
         stage_plain<uint8_t, BU8_W>(IB, ms, jd->pb, jd->h, jd->w, x0 - 16, y0 - 1, NT);
-        if (need_m) stage_plain<uint8_t, BU8_W>(JBm, mk, jd->pa, jd->h, jd->w, x0 - 16, y0 - 1, NT);
-        if (need_o) stage_plain<uint8_t, BU8_W>(JBo, out, jd->po, jd->h, jd->w, x0 - 16, y0 - 1, NT);
+        stage_plain<uint8_t, BU8_W>(JB, jsrc, jpitch, jd->h, jd->w, x0 - 16, y0 - 1, NT);
         __syncthreads();
     }
-    // working copy (word copies; each word lies in one column region, words
-    // 0 and 17 being the left / right halo columns).  Cells outside the
-    // image are zero in both J and I (zero fill) and so never raise or get
-    // raised.
+    // working copy (word copies; word 18 of a row is padding).  Cells
+    // outside the image are zero in J and I (zero fill) and so never raise
+    // or get raised.
     {
-        const uint32_t *I32 = (const uint32_t *)IB, *M32 = (const uint32_t *)JBm, *O32 = (const uint32_t *)JBo;
+        const uint32_t *I32 = (const uint32_t *)IB, *J32 = (const uint32_t *)JB;
         uint32_t *JW32 = (uint32_t *)JW, *IW32 = (uint32_t *)IW;
         for (int i = tid; i < RR * 19; i += NT) {
             const int r = i / 19, k = i - r * 19;
-            if (k == 18) {
-                JW32[i] = 0;
-                IW32[i] = 0;
-                continue;
-            }
-            const int reg = region(r) * 3 + (k == 0 ? 0 : (k == 17 ? 2 : 1));
-            IW32[i] = I32[r * 24 + 3 + k];
-            JW32[i] = hdr[H_SRC + reg] == 1 ? O32[r * 24 + 3 + k] : M32[r * 24 + 3 + k];
+            IW32[i] = k == 18 ? 0u : I32[r * 24 + 3 + k];
+            JW32[i] = k == 18 ? 0u : J32[r * 24 + 3 + k];
         }
     }
     __syncthreads();
-    // clip marker values by the mask where no later step does it: the halo
-    // ring always (halo pixels are sources only), the interior on a first
-    // visit without sweeps (the first row pass clips every interior pixel)
+    // halo cells of neighbour tiles whose J lives in the other buffer
+    // (marker vs current result) are read directly; marker values are then
+    // clipped by the mask everywhere no later step does it: the halo ring
+    // always (halo pixels are sources only), the interior on a first visit
+    // without sweeps (the first row pass clips every interior pixel)
     for (int k = tid; k < 4 * (TS + 1); k += NT) {
         int r, c;
         halo_cell(k, r, c);
         const int i = U8Grid::cell(r, c);
+        const int src = hdr[H_SRC + region(r) * 3 + region(c)];
+        if (src != 2 && src != (first ? 0 : 1)) {
+            const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+            if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w)
+                JW[i] = src == 1 ? __ldcg(out + (int64_t)gy * jd->po + gx) : __ldcg(mk + (int64_t)gy * jd->pa + gx);
+        }
         if (JW[i] > IW[i]) JW[i] = IW[i];
     }
     if (first && ka.sweeps == 0)
@@ -684,14 +706,17 @@ __device__ bool recon_u8_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
         }
     __syncthreads();
 
+    pc.mark(hdr, 0);
     U8Grid g{JW, IW};
     const int *off = hdr + H_OFF;
 
     // 2. sweeps, 3. seeds + propagation
-    recon_propagate<CONN, NT>(ka, g, hdr, Q0, Q1, first, off);
+    recon_propagate<CONN, NT>(ka, g, hdr, Q0, Q1, first, off, pc);
     __syncthreads();
 
-    // 4. store the interior rows (16-byte vector stores when aligned)
+    // 4. store the interior rows (16-byte vector stores when aligned); the
+    //    neighbourhood states for the border test are fetched meanwhile
+    load_sources(ka, jd, tx, ty, hdr);
     {
         const bool vec = jd->use_tma != 0;  // TMA maps imply 16-byte aligned base and pitch
         for (int i = tid; i < TS * 4; i += NT) {
@@ -709,12 +734,11 @@ __device__ bool recon_u8_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
         }
     }
     __syncthreads();
-    if (tid == 0) __threadfence();
-    load_sources(ka, jd, tx, ty, hdr);  // fresh states for the border test
-    __syncthreads();
+    publish_tile(ka, gt, hdr);
     recon_border<uint8_t, CONN, NT>(jd, g, hdr, x0, y0);
     __syncthreads();
-    if (tid == 0) finish_tile(ka, jd, gt, tx, ty, hdr);
+    finish_tile(ka, jd, gt, tx, ty, hdr);
+    pc.mark(hdr, 3);
     return true;
 }
 
@@ -733,6 +757,8 @@ __device__ bool recon_i32_visit(const KArgs &ka, const JobDesc *jd, int gt, char
     const int *mk = (const int *)jd->a, *ms = (const int *)jd->b;
     int *out = (int *)jd->out;
 
+    PhaseClock pc;
+    pc.start();
     load_sources(ka, jd, tx, ty, hdr);
     begin_visit(hdr);
     make_offsets<CONN, BI32_W>(hdr);
@@ -776,22 +802,23 @@ __device__ bool recon_i32_visit(const KArgs &ka, const JobDesc *jd, int gt, char
     }
     __syncthreads();
 
+    pc.mark(hdr, 0);
     I32Grid g{JB, IB};
     const int *off = hdr + H_OFF;
-    recon_propagate<CONN, NT>(ka, g, hdr, Q0, Q1, first, off);
+    recon_propagate<CONN, NT>(ka, g, hdr, Q0, Q1, first, off, pc);
     __syncthreads();
+    load_sources(ka, jd, tx, ty, hdr);
     for (int i = tid; i < TS * TS; i += NT) {
         const int r = i / TS, c = i - r * TS;
         const int gy = y0 + r, gx = x0 + c;
         if (gy < jd->h && gx < jd->w) out[(int64_t)gy * jd->po + gx] = JB[I32Grid::cell(r + 1, c + 1)];
     }
     __syncthreads();
-    if (tid == 0) __threadfence();
-    load_sources(ka, jd, tx, ty, hdr);
-    __syncthreads();
+    publish_tile(ka, gt, hdr);
     recon_border<int, CONN, NT>(jd, g, hdr, x0, y0);
     __syncthreads();
-    if (tid == 0) finish_tile(ka, jd, gt, tx, ty, hdr);
+    finish_tile(ka, jd, gt, tx, ty, hdr);
+    pc.mark(hdr, 3);
     return true;
 }
 
@@ -894,6 +921,8 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     const int x0 = tx * TS, y0 = ty * TS;
     const int oy = y0 - 1, ox = x0 - 1;
 
+    PhaseClock pc;
+    pc.start();
     load_sources(ka, jd, tx, ty, hdr);
     begin_visit(hdr);
     make_offsets<8, WE_P>(hdr);
@@ -938,6 +967,7 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
         W[r * WE_P + c] = v;
     }
     __syncthreads();
+    pc.mark(hdr, 0);
     const int *off = hdr + H_OFF;
 
     // 2. seeds: every staged pixel that can improve an interior neighbour on
@@ -946,6 +976,7 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, QCAP_E, ka.spill_cap};
     const unsigned seeds = edt_seed_scan<NT>(W, oy, ox, q0, first, off);
     if ((tid & 31) == 0) atomicAdd(hdr + H_SEEDS, (int)seeds);
+    pc.mark(hdr, 1);
 
     // 3. propagation rounds
     auto proc = [&](int p) -> unsigned {
@@ -962,8 +993,10 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     auto rescan = [&](const RQ &q) -> unsigned { return edt_seed_scan<NT>(W, oy, ox, q, true, off); };
     run_rounds<NT>(hdr, Q0, Q1, QCAP_E, spill, ka.spill_cap, off, proc, rescan);
     __syncthreads();
+    pc.mark(hdr, 2);
 
     // 4. store nearest (linear index) and squared distance
+    load_sources(ka, jd, tx, ty, hdr);
     for (int i = tid; i < TS * TS; i += NT) {
         const int r = i / TS, c = i - r * TS;
         const int gy = y0 + r, gx = x0 + c;
@@ -980,9 +1013,7 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
         }
     }
     __syncthreads();
-    if (tid == 0) __threadfence();
-    load_sources(ka, jd, tx, ty, hdr);
-    __syncthreads();
+    publish_tile(ka, gt, hdr);
 
     // 5. border test (strict distance rule across tiles)
     for (int k = tid; k < 4 * (TS + 1); k += NT) {
@@ -1003,7 +1034,8 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
         if (need) hdr[H_FLAG + reg] = 1;
     }
     __syncthreads();
-    if (tid == 0) finish_tile(ka, jd, gt, tx, ty, hdr);
+    finish_tile(ka, jd, gt, tx, ty, hdr);
+    pc.mark(hdr, 3);
     return true;
 }
 
@@ -1060,6 +1092,7 @@ __global__ void __launch_bounds__(FAM_NT[FAM]) persistent_kernel(const __grid_co
             atomicAdd(&ka.ctl->spills, (unsigned long long)hdr[H_SPILL]);
             atomicAdd(&ka.ctl->rescans, (unsigned long long)hdr[H_RESC]);
             atomicAdd(&ka.ctl->rounds, (unsigned long long)hdr[H_ROUNDS]);
+            for (int i = 0; i < 4; ++i) atomicAdd(&ka.ctl->phase_ns[i], (unsigned long long)(unsigned)hdr[H_PH + i]);
             __threadfence();
             atomicSub(ka.tq.pending, 1);
         }
