@@ -29,7 +29,7 @@ struct iwpp_ctx {
     uint64_t launches = 0;
     uint64_t kernel_ns = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending_events, free_events;
-    int occupancy[FAM_COUNT] = {0, 0, 0, 0};  // blocks per SM per kernel family
+    int occupancy[FAM_COUNT] = {};  // blocks per SM per kernel family
     std::map<uint64_t, iwpp_options> tuned;   // autotuner results by workload key
 };
 

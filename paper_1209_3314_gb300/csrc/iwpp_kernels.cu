@@ -45,7 +45,7 @@ namespace iwpp {
 constexpr int TS = TILE;       // 64
 constexpr int RR = TS + 2;     // staged rows / columns
 constexpr int QCAP_R = 2048;   // reconstruction block-queue entries per buffer
-constexpr int QCAP_E = 4096;   // distance-transform block-queue entries per buffer
+constexpr int QCAP_E = 2048;   // distance-transform block-queue entries per buffer
 
 // u8 TMA box: columns x0-16 .. x0+79 (96), rows y0-1 .. y0+64 (66)
 constexpr int BU8_W = 96, BU8_BYTES = BU8_W * RR, BU8_PAD = 6400;
@@ -56,8 +56,8 @@ constexpr int BI32_W = 72, BI32_BYTES = BI32_W * RR * 4, BI32_PAD = 19072;
 // r*76 + c + 3, so that word k of a row holds cells 4k-3 .. 4k and box word
 // k+3 maps onto working word k.
 constexpr int WU8_P = 76, WU8_PAD = 5120;
-// distance-transform working array: 64-bit words, row stride 67
-constexpr int WE_P = 67, WE_PAD = 35456;
+// distance-transform working array: the int32 TMA box layout (stride 72,
+// cell (r, c) at word r*72 + c + 3), holding packed feature coordinates
 
 // shared header (ints)
 enum : int {
@@ -75,15 +75,14 @@ constexpr int RU8_JW = HDR_BYTES, RU8_IW = RU8_JW + WU8_PAD, RU8_U = RU8_IW + WU
 constexpr int RU8_BYTES = RU8_U + 2 * BU8_PAD;
 constexpr int RI32_J = HDR_BYTES, RI32_I = RI32_J + BI32_PAD, RI32_U = RI32_I + BI32_PAD;
 constexpr int RI32_BYTES = RI32_U + BI32_PAD;
-constexpr int E_W = HDR_BYTES, E_U = E_W + WE_PAD;
-constexpr int E_BYTES = E_U + BU8_PAD + BI32_PAD;
+constexpr int E_W = HDR_BYTES, E_U = E_W + BI32_PAD;
+constexpr int E_BYTES = E_U + 2 * QCAP_E * 2;
 static_assert(RU8_U % 128 == 0 && RI32_J % 128 == 0 && RI32_I % 128 == 0 && RI32_U % 128 == 0 &&
-                  E_U % 128 == 0 && (E_U + BU8_PAD) % 128 == 0,
+                  E_U % 128 == 0 && E_W % 128 == 0,
               "TMA destinations must be 128-byte aligned");
 static_assert(2 * QCAP_R * 2 <= 2 * BU8_PAD && 2 * QCAP_R * 2 <= BI32_PAD &&
-                  2 * QCAP_E * 2 <= BU8_PAD + BI32_PAD,
+                  BU8_PAD <= 2 * QCAP_E * 2,
               "queues must fit the staging union");
-static_assert(RR * WE_P * 8 <= WE_PAD, "EDT working array");
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int FAM_SMEM[FAM_COUNT] = {RU8_BYTES, RI32_BYTES, E_BYTES,
@@ -158,6 +157,7 @@ __device__ __forceinline__ void finish_tile(const KArgs &ka, const JobDesc *jd, 
     if (k < 9 && k != 4 && hdr[H_FLAG + k]) {
         __threadfence();
         tq_push(ka.tq, ka.ctl, jd->tile_base + (ty + k / 3 - 1) * jd->tiles_x + tx + k % 3 - 1);
+        __threadfence();  // the push is performed before the caller's pending decrement
     }
     __syncthreads();
     if (k == 0) tq_finish(ka.tq, ka.ctl, gt);
@@ -240,11 +240,19 @@ __device__ __forceinline__ unsigned warp_enqueue(unsigned mask, int p, const int
 // rescan(q): re-seeds the whole tile into q, returns the count.
 template <int NT, typename Proc, typename Rescan>
 __device__ void run_rounds(int *hdr, uint16_t *Q0, uint16_t *Q1, int qcap, uint16_t *spill, int spill_cap,
-                           const int *off, Proc proc, Rescan rescan) {
+                           const int *off, Proc proc, Rescan rescan, unsigned long long deadline, Control *ctl) {
     const int tid = threadIdx.x;
     int cur = 0;
     unsigned pushed = 0, spilled = 0, rescans = 0, rounds = 0;
     while (true) {
+        // every round makes progress, so the loop ends; the deadline is a
+        // last guard that turns a defect into a reported timeout
+        if (tid == 0 && (rounds & 63) == 63 && globaltimer_ns() > deadline) {
+            atomicOr(&ctl->status, ST_TIMEOUT);
+            atomicOr(&ctl->sticky, ST_TIMEOUT);
+            hdr[H_CNT0 + cur] = 0;
+            hdr[H_RESCAN] = 0;
+        }
         __syncthreads();
         const int n_raw = hdr[H_CNT0 + cur];
         const int resc = hdr[H_RESCAN];
@@ -556,7 +564,7 @@ __device__ unsigned halo_seed(const G &g, const RQ &q, const int *off) {
 
 template <int CONN, int NT, typename G>
 __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t *Q0, uint16_t *Q1, bool first,
-                                const int *off, PhaseClock &pc) {
+                                const int *off, PhaseClock &pc, unsigned long long deadline) {
     uint16_t *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
     RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, QCAP_R, ka.spill_cap};
     auto sweeps_then_dilate = [&](const RQ &q) -> unsigned {
@@ -599,7 +607,7 @@ __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t 
         return m;
     };
     auto rescan = [&](const RQ &q) -> unsigned { return g.template dilate<CONN, NT>(q, off); };
-    run_rounds<NT>(hdr, Q0, Q1, QCAP_R, spill, ka.spill_cap, off, proc, rescan);
+    run_rounds<NT>(hdr, Q0, Q1, QCAP_R, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl);
     pc.mark(hdr, 2);
 }
 
@@ -711,7 +719,7 @@ __device__ bool recon_u8_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
     const int *off = hdr + H_OFF;
 
     // 2. sweeps, 3. seeds + propagation
-    recon_propagate<CONN, NT>(ka, g, hdr, Q0, Q1, first, off, pc);
+    recon_propagate<CONN, NT>(ka, g, hdr, Q0, Q1, first, off, pc, deadline);
     __syncthreads();
 
     // 4. store the interior rows (16-byte vector stores when aligned); the
@@ -805,7 +813,7 @@ __device__ bool recon_i32_visit(const KArgs &ka, const JobDesc *jd, int gt, char
     pc.mark(hdr, 0);
     I32Grid g{JB, IB};
     const int *off = hdr + H_OFF;
-    recon_propagate<CONN, NT>(ka, g, hdr, Q0, Q1, first, off, pc);
+    recon_propagate<CONN, NT>(ka, g, hdr, Q0, Q1, first, off, pc, deadline);
     __syncthreads();
     load_sources(ka, jd, tx, ty, hdr);
     for (int i = tid; i < TS * TS; i += NT) {
@@ -824,54 +832,70 @@ __device__ bool recon_i32_visit(const KArgs &ka, const JobDesc *jd, int gt, char
 
 // =====================================================================
 // Distance transform (Section 2.2; Algorithms 3 and 6).  Each staged pixel
-// holds one 64-bit word: squared distance to its assigned feature in the
-// high half, the feature's packed coordinates (y << 16 | x) in the low half;
-// all ones is the virtual 'inf' pixel.  Propagating feature f to q is one
-// atomicMin of (d2(q, f) << 32 | f): the word only decreases, so q takes f
-// exactly when f is strictly closer, or equally close with smaller
-// coordinates (a fixed tie rule in place of the arrival order).
+// holds VR, the packed coordinates (y << 16 | x) of its assigned feature;
+// all ones is the virtual 'inf' pixel, farther than any real pixel.  VR(q)
+// takes feature f when f is strictly closer, or equally close with smaller
+// packed coordinates (a fixed tie rule in place of the arrival order); the
+// update is Algorithm 6's compare-and-swap loop.
 // =====================================================================
 
-constexpr unsigned long long W_INF = ~0ull;
+constexpr unsigned VR_INF = 0xFFFFFFFFu;
 
 __device__ __forceinline__ unsigned pack_yx(int y, int x) { return ((unsigned)y << 16) | (unsigned)x; }
 
-__device__ __forceinline__ unsigned long long cand(int y, int x, unsigned f) {
+// squared distance from (y, x) to packed feature f (f != VR_INF)
+__device__ __forceinline__ unsigned d2(int y, int x, unsigned f) {
     const int dy = y - (int)(f >> 16), dx = x - (int)(f & 0xFFFFu);
-    return ((unsigned long long)(unsigned)(dy * dy + dx * dx) << 32) | f;
+    return (unsigned)(dy * dy + dx * dx);
+}
+
+// does feature f (distance dn from q) beat q's current feature c?
+__device__ __forceinline__ bool better(unsigned dn, unsigned f, int qy, int qx, unsigned c) {
+    if (c == VR_INF) return true;
+    const unsigned dc = d2(qy, qx, c);
+    return dn < dc || (dn == dc && f < c);
 }
 
 __device__ __forceinline__ bool is_feature(uint8_t b, int flags) { return (flags & 1) ? b != 0 : b == 0; }
 
-// current word of image pixel (gy, gx) read from global memory
-__device__ __forceinline__ unsigned long long w_fetch(const JobDesc *jd, bool visited, int gy, int gx) {
+// current VR of image pixel (gy, gx) read from global memory
+__device__ __forceinline__ unsigned vr_fetch(const JobDesc *jd, bool visited, int gy, int gx) {
     if (visited) {
         const int idx = __ldcg(jd->nearest + (int64_t)gy * jd->w + gx);
-        if (idx < 0) return W_INF;
+        if (idx < 0) return VR_INF;
         const int fy = idx / jd->w;
-        return cand(gy, gx, pack_yx(fy, idx - fy * jd->w));
+        return pack_yx(fy, idx - fy * jd->w);
     }
     const uint8_t b = __ldcg((const uint8_t *)jd->a + (int64_t)gy * jd->pa + gx);
-    return is_feature(b, jd->flags) ? cand(gy, gx, pack_yx(gy, gx)) : W_INF;
+    return is_feature(b, jd->flags) ? pack_yx(gy, gx) : VR_INF;
 }
 
-// Can the feature f of cell (pr, pc) improve its interior neighbour n?  With
-// commit, performs the update and reports whether this call made it.
-__device__ __forceinline__ bool edt_try(unsigned long long *W, int oy, int ox, int pr, int pc, unsigned f, int n,
+constexpr int EP = BI32_W;  // VR row stride (words)
+__device__ __forceinline__ int ecell(int r, int c) { return r * EP + c + 3; }
+
+// Can the feature of cell (pr, pc) improve its interior neighbour n?  With
+// commit, performs the compare-and-swap update and reports whether this call
+// made it.
+__device__ __forceinline__ bool edt_try(unsigned *V, int oy, int ox, int pr, int pc, unsigned f, int n,
                                         bool commit) {
     const int rr = pr + nb_dy(8, n), cc = pc + nb_dx(8, n);
     if (rr < 1 || rr > TS || cc < 1 || cc > TS) return false;
-    const int qi = rr * WE_P + cc;
-    const unsigned long long wq = ((volatile unsigned long long *)W)[qi];
-    if ((wq >> 32) == 0) return false;  // a feature is its own nearest feature
-    const unsigned long long cv = cand(oy + rr, ox + cc, f);
-    if (cv >= wq) return false;
-    if (!commit) return true;
-    return atomicMin(W + qi, cv) > cv;
+    const int qi = ecell(rr, cc);
+    const int qy = oy + rr, qx = ox + cc;
+    const unsigned self = pack_yx(qy, qx);
+    const unsigned dn = d2(qy, qx, f);
+    unsigned c = ((volatile unsigned *)V)[qi];
+    while (true) {
+        if (c == self || !better(dn, f, qy, qx, c)) return false;  // a feature is its own nearest
+        if (!commit) return true;
+        const unsigned old = atomicCAS(V + qi, c, f);
+        if (old == c) return true;
+        c = old;
+    }
 }
 
 template <int NT>
-__device__ unsigned edt_seed_scan(unsigned long long *W, int oy, int ox, const RQ &q, bool all, const int *off) {
+__device__ unsigned edt_seed_scan(unsigned *V, int oy, int ox, const RQ &q, bool all, const int *off) {
     unsigned pushed = 0;
     const int ncell = all ? RR * RR : 4 * (TS + 1);
     for (int base = 0; base < ncell; base += NT) {
@@ -882,23 +906,23 @@ __device__ unsigned edt_seed_scan(unsigned long long *W, int oy, int ox, const R
             int r, c;
             if (all) { r = k / RR; c = k - r * RR; }
             else halo_cell(k, r, c);
-            i = r * WE_P + c;
-            const unsigned long long w = W[i];
-            if (w != W_INF) {
-                const unsigned f = (unsigned)w;
-                if ((w >> 32) == 0) {
-                    // a feature improves exactly its interior neighbours
-                    // that are not features themselves
+            i = ecell(r, c);
+            const unsigned f = V[i];
+            if (f != VR_INF) {
+                if (f == pack_yx(oy + r, ox + c)) {
+                    // a feature improves exactly its interior neighbours that
+                    // are not features themselves
 #pragma unroll
                     for (int n = 0; n < 8; ++n) {
                         const int rr = r + nb_dy(8, n), cc = c + nb_dx(8, n);
-                        if (rr >= 1 && rr <= TS && cc >= 1 && cc <= TS && (W[rr * WE_P + cc] >> 32) != 0)
+                        if (rr >= 1 && rr <= TS && cc >= 1 && cc <= TS &&
+                            V[ecell(rr, cc)] != pack_yx(oy + rr, ox + cc))
                             m = 1u << 8;
                     }
                 } else {
 #pragma unroll
                     for (int n = 0; n < 8; ++n)
-                        if (edt_try(W, oy, ox, r, c, f, n, false)) m = 1u << 8;
+                        if (edt_try(V, oy, ox, r, c, f, n, false)) m = 1u << 8;
                 }
             }
         }
@@ -912,9 +936,8 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
                           unsigned long long deadline) {
     int *hdr = (int *)sm;
     uint64_t *bar = (uint64_t *)(sm + 256);
-    unsigned long long *W = (unsigned long long *)(sm + E_W);
-    uint8_t *BB = (uint8_t *)(sm + E_U);
-    int *NB = (int *)(sm + E_U + BU8_PAD);
+    unsigned *V = (unsigned *)(sm + E_W);  // also the landing zone of the nearest box
+    uint8_t *BB = (uint8_t *)(sm + E_U);   // binary box (then the queues)
     uint16_t *Q0 = (uint16_t *)(sm + E_U), *Q1 = Q0 + QCAP_E;
     const int tid = threadIdx.x;
     const int lt = gt - jd->tile_base, tx = lt % jd->tiles_x, ty = lt / jd->tiles_x;
@@ -925,7 +948,7 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     pc.start();
     load_sources(ka, jd, tx, ty, hdr);
     begin_visit(hdr);
-    make_offsets<8, WE_P>(hdr);
+    make_offsets<8, EP>(hdr);
     __syncthreads();
     int need_b = 0, need_n = 0;
 #pragma unroll
@@ -939,32 +962,35 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, need_b * BU8_BYTES + need_n * BI32_BYTES);
             if (need_b) tma_load_2d(BB, &jd->tm[0], x0 - 16, oy, bar);
-            if (need_n) tma_load_2d(NB, &jd->tm[2], x0 - 4, oy, bar);
+            if (need_n) tma_load_2d(V, &jd->tm[2], x0 - 4, oy, bar);
         }
         if (!wait_boxes(bar, phase, deadline, ka.ctl)) return false;
     } else {
         if (need_b)
             stage_plain<uint8_t, BU8_W>(BB, (const uint8_t *)jd->a, jd->pa, jd->h, jd->w, x0 - 16, oy, NT);
-        if (need_n) stage_plain<int, BI32_W>(NB, jd->nearest, jd->w, jd->h, jd->w, x0 - 4, oy, NT);
+        if (need_n) stage_plain<int, BI32_W>((int *)V, jd->nearest, jd->w, jd->h, jd->w, x0 - 4, oy, NT);
         __syncthreads();
     }
-    // 1. working words of tile + halo
-    for (int i = tid; i < RR * RR; i += NT) {
-        const int r = i / RR, c = i - r * RR;
+    // 1. VR of tile + halo, converted in place: linear nearest indices of
+    //    visited regions -> packed coordinates; unvisited regions from the
+    //    binary image (Algorithm 6 initialisation); outside the image 'inf'
+    for (int i = tid; i < RR * EP; i += NT) {
+        const int r = i / EP, c = i - r * EP - 3;
+        if (c < 0 || c >= RR) continue;
         const int gy = oy + r, gx = ox + c;
-        unsigned long long v = W_INF;
+        unsigned v = VR_INF;
         if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
             if (hdr[H_SRC + region(r) * 3 + region(c)] == 1) {
-                const int idx = NB[r * BI32_W + c + 3];
+                const int idx = (int)V[i];
                 if (idx >= 0) {
                     const int fy = idx / jd->w;
-                    v = cand(gy, gx, pack_yx(fy, idx - fy * jd->w));
+                    v = pack_yx(fy, idx - fy * jd->w);
                 }
             } else if (is_feature(BB[r * BU8_W + c + 15], jd->flags)) {
-                v = cand(gy, gx, pack_yx(gy, gx));
+                v = pack_yx(gy, gx);
             }
         }
-        W[r * WE_P + c] = v;
+        V[i] = v;
     }
     __syncthreads();
     pc.mark(hdr, 0);
@@ -974,42 +1000,41 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     //    a first visit, only the halo on later visits
     uint16_t *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
     RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, QCAP_E, ka.spill_cap};
-    const unsigned seeds = edt_seed_scan<NT>(W, oy, ox, q0, first, off);
+    const unsigned seeds = edt_seed_scan<NT>(V, oy, ox, q0, first, off);
     if ((tid & 31) == 0) atomicAdd(hdr + H_SEEDS, (int)seeds);
     pc.mark(hdr, 1);
 
     // 3. propagation rounds
     auto proc = [&](int p) -> unsigned {
-        const unsigned long long w = ((volatile unsigned long long *)W)[p];
-        if (w == W_INF) return 0u;
-        const unsigned f = (unsigned)w;
-        const int pr = p / WE_P, pc = p - pr * WE_P;
+        const unsigned f = ((volatile unsigned *)V)[p];
+        if (f == VR_INF) return 0u;
+        const int pr = p / EP, pc2 = p - pr * EP - 3;
         unsigned m = 0;
 #pragma unroll
         for (int n = 0; n < 8; ++n)
-            if (edt_try(W, oy, ox, pr, pc, f, n, true)) m |= 1u << n;
+            if (edt_try(V, oy, ox, pr, pc2, f, n, true)) m |= 1u << n;
         return m;
     };
-    auto rescan = [&](const RQ &q) -> unsigned { return edt_seed_scan<NT>(W, oy, ox, q, true, off); };
-    run_rounds<NT>(hdr, Q0, Q1, QCAP_E, spill, ka.spill_cap, off, proc, rescan);
+    auto rescan = [&](const RQ &q) -> unsigned { return edt_seed_scan<NT>(V, oy, ox, q, true, off); };
+    run_rounds<NT>(hdr, Q0, Q1, QCAP_E, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl);
     __syncthreads();
     pc.mark(hdr, 2);
 
-    // 4. store nearest (linear index) and squared distance
+    // 4. store nearest (linear index) and squared distance; the
+    //    neighbourhood states for the border test are fetched meanwhile
     load_sources(ka, jd, tx, ty, hdr);
     for (int i = tid; i < TS * TS; i += NT) {
         const int r = i / TS, c = i - r * TS;
         const int gy = y0 + r, gx = x0 + c;
         if (gy >= jd->h || gx >= jd->w) continue;
-        const unsigned long long w = W[(r + 1) * WE_P + c + 1];
+        const unsigned f = V[ecell(r + 1, c + 1)];
         const int64_t o = (int64_t)gy * jd->w + gx;
-        if (w == W_INF) {
+        if (f == VR_INF) {
             jd->nearest[o] = -1;
             jd->sqdist[o] = INT_MAX;
         } else {
-            const unsigned f = (unsigned)w;
             jd->nearest[o] = (int)(f >> 16) * jd->w + (int)(f & 0xFFFFu);
-            jd->sqdist[o] = (int)(w >> 32);
+            jd->sqdist[o] = (int)d2(gy, gx, f);
         }
     }
     __syncthreads();
@@ -1022,14 +1047,15 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
         const int gy = oy + r, gx = ox + c;
         if (gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w) continue;
         const int reg = region(r) * 3 + region(c);
-        const unsigned dq = (unsigned)(w_fetch(jd, hdr[H_SRC + reg] == 1, gy, gx) >> 32);
+        const unsigned cq = vr_fetch(jd, hdr[H_SRC + reg] == 1, gy, gx);
+        const unsigned dq = cq == VR_INF ? VR_INF : d2(gy, gx, cq);
         bool need = false;
 #pragma unroll
         for (int n = 0; n < 8; ++n) {
-            const int pr = r + nb_dy(8, n), pc = c + nb_dx(8, n);
-            if (pr < 1 || pr > TS || pc < 1 || pc > TS) continue;
-            const unsigned long long wp = W[pr * WE_P + pc];
-            if (wp != W_INF && (unsigned)(cand(gy, gx, (unsigned)wp) >> 32) < dq) need = true;
+            const int pr = r + nb_dy(8, n), pcc = c + nb_dx(8, n);
+            if (pr < 1 || pr > TS || pcc < 1 || pcc > TS) continue;
+            const unsigned fp = V[ecell(pr, pcc)];
+            if (fp != VR_INF && d2(gy, gx, fp) < dq) need = true;
         }
         if (need) hdr[H_FLAG + reg] = 1;
     }
@@ -1188,7 +1214,11 @@ cudaError_t family_occupancy(int fam, int *n) {
     }
 }
 
+// Each launch helper first clears the calling thread's last-error slot: a
+// status such as cudaErrorNotReady left there by an earlier query (e.g. an
+// event poll) must not be mistaken for a failure of this launch.
 cudaError_t launch_init(const KArgs &ka, int first_attempt, cudaStream_t s) {
+    (void)cudaGetLastError();
     int blocks = (int)((ka.tq.cap + 255) / 256);
     blocks = blocks > 4096 ? 4096 : (blocks < 1 ? 1 : blocks);
     fill_queue_kernel<<<blocks, 256, 0, s>>>(ka, first_attempt);
@@ -1201,6 +1231,7 @@ static void launch_fam(const KArgs &ka, int grid, cudaStream_t s) {
 }
 
 cudaError_t launch_persistent(const KArgs &ka, int fam, int grid, cudaStream_t s) {
+    (void)cudaGetLastError();
     switch (fam) {
         case FAM_RECON_U8: launch_fam<FAM_RECON_U8>(ka, grid, s); break;
         case FAM_RECON_I32: launch_fam<FAM_RECON_I32>(ka, grid, s); break;
@@ -1212,6 +1243,7 @@ cudaError_t launch_persistent(const KArgs &ka, int fam, int grid, cudaStream_t s
 }
 
 cudaError_t launch_decide(const KArgs &ka, int final_step, cudaStream_t s) {
+    (void)cudaGetLastError();
     decide_kernel<<<1, 1, 0, s>>>(ka, final_step);
     return cudaGetLastError();
 }
