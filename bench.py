@@ -264,7 +264,8 @@ def bench_batched(ctx, dev, n, reps):
             "mpx_s": round(px / ms / 1e3, 1), "one_per_launch_ms": round(base_ms, 3),
             "one_per_launch_imgs_s": round(n / base_ms * 1e3, 1), "speedup": round(base_ms / ms, 2),
             "launch": "one persistent launch per batch, CUDA graph replay, autotuned",
-            "tuned": {k: tuned[k] for k in ("sweeps", "revisit_sweep_min", "blocks_per_sm")}}
+            "tuned": {k: tuned[k] for k in ("sweeps", "revisit_sweep_min", "edt_sweeps", "edt_revisit_sweep_min",
+                                                 "blocks_per_sm")}}
 
 
 def bench_served(ctx, dev, rates, duration, budget):

@@ -97,7 +97,11 @@ typedef struct {
     int32_t revisit_sweep_min; /* reconstruction: a later visit of a tile runs
                                 the sweeps when more halo pixels than this can
                                 propagate inward, else only the queue       */
-    int32_t reserved[7];
+    int32_t edt_sweeps;      /* distance transform: vector-propagation sweep
+                                sets per bulk visit (0 = queue only)          */
+    int32_t edt_revisit_sweep_min; /* distance transform: a later visit sweeps
+                                when more halo pixels than this changed       */
+    int32_t reserved[5];
 } iwpp_options;
 
 /* Creates a context on `device`.  hbm_budget_bytes bounds the workspace the

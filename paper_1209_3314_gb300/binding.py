@@ -48,7 +48,8 @@ class Options(ctypes.Structure):
                 ("sweeps", ctypes.c_int32), ("queue_factor", ctypes.c_int32),
                 ("spill_cap", ctypes.c_int32), ("max_relaunch", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("revisit_sweep_min", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("revisit_sweep_min", ctypes.c_int32), ("edt_sweeps", ctypes.c_int32),
+                ("edt_revisit_sweep_min", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class Request(ctypes.Structure):

@@ -236,6 +236,8 @@ int prepare(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, const iwpp_options &opt, 
     ka.spill_cap = std::max(0, opt.spill_cap);
     ka.sweeps = opt.sweeps;
     ka.revisit_sweep_min = opt.revisit_sweep_min;
+    ka.edt_sweeps = opt.edt_sweeps;
+    ka.edt_revisit_sweep_min = opt.edt_revisit_sweep_min;
     ka.timeout_ns = (unsigned long long)opt.timeout_ms * 1000000ull;
     return IWPP_OK;
 }
@@ -460,6 +462,8 @@ int iwpp_ctx_create(iwpp_ctx **out, int device, size_t hbm_budget_bytes) {
     ctx->opt.max_relaunch = 1;
     ctx->opt.timeout_ms = 10000;
     ctx->opt.revisit_sweep_min = 0;
+    ctx->opt.edt_sweeps = 1;
+    ctx->opt.edt_revisit_sweep_min = 64;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&ctx->ctl, sizeof(Control)) != cudaSuccess ||
@@ -501,7 +505,7 @@ int iwpp_set_options(iwpp_ctx *ctx, const iwpp_options *o) {
     if (o->blocks_per_sm < 0 || o->sweeps < 0 || o->sweeps > 64 || o->queue_factor < 1 || o->queue_factor > 4096 ||
         o->spill_cap < 0 || o->spill_cap > (1 << 20) || o->max_relaunch < 0 || o->max_relaunch > 64 ||
         o->timeout_ms < 1 || o->timeout_ms > 600000 || o->timing < 0 || o->timing > 1 ||
-        o->revisit_sweep_min < 0)
+        o->revisit_sweep_min < 0 || o->edt_sweeps < 0 || o->edt_sweeps > 64 || o->edt_revisit_sweep_min < 0)
         return fail(ctx, IWPP_EINVAL, "option out of range");
     ctx->opt = *o;
     return IWPP_OK;
@@ -754,16 +758,26 @@ int iwpp_plan_autotune(iwpp_plan *p, void *stream, int reps, iwpp_options *best)
     float best_ms = 1e30f;
     int rc = IWPP_OK;
     const int occ = ctx->occupancy[p->P.fam];
+    // sweep candidates per operation; a mixed plan pairs them up
     const int sweeps_c[3] = {1, 2, 3};
     const int revisit_c[2] = {0, 32};
+    const int edt_sweeps_c[3] = {0, 1, 2};
+    const int edt_revisit_c[2] = {16, 64};
+    const int fam = p->P.fam;
     const int bps_c[2] = {0, occ > 2 ? occ - 1 : 0};
     for (int a = 0; a < 3 && rc == IWPP_OK; ++a)
         for (int b = 0; b < 2 && rc == IWPP_OK; ++b)
             for (int c = 0; c < 2 && rc == IWPP_OK; ++c) {
                 if (c == 1 && bps_c[1] == 0) continue;
                 iwpp_options o = base;
-                o.sweeps = sweeps_c[a];
-                o.revisit_sweep_min = revisit_c[b];
+                if (fam != FAM_EDT) {
+                    o.sweeps = sweeps_c[a];
+                    o.revisit_sweep_min = revisit_c[b];
+                }
+                if (fam == FAM_EDT || fam == FAM_MIXED) {
+                    o.edt_sweeps = edt_sweeps_c[a];
+                    o.edt_revisit_sweep_min = edt_revisit_c[b];
+                }
                 o.blocks_per_sm = bps_c[c];
                 if ((rc = plan_prepare(p, o))) break;
                 if ((rc = iwpp_plan_launch(p, st))) break;  // warm-up

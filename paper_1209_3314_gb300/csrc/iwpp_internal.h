@@ -46,6 +46,8 @@ struct alignas(64) KArgs {
     int spill_cap;
     int sweeps;           // raster + anti-raster sweep sets per bulk visit
     int revisit_sweep_min;  // later visits sweep when more halo seeds than this
+    int edt_sweeps;       // the same two settings for the distance transform
+    int edt_revisit_sweep_min;
     unsigned long long timeout_ns;
 };
 

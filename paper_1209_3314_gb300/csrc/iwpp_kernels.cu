@@ -236,9 +236,9 @@ __device__ __forceinline__ unsigned warp_enqueue(unsigned mask, int p, const int
 }
 
 // Propagation rounds until the queue is empty (the loop of Algorithm 4).
-// proc(p): processes item p, returns the mask of neighbours it raised;
+// proc(p, n): tests / updates neighbour n of item p, true if it raised it;
 // rescan(q): re-seeds the whole tile into q, returns the count.
-template <int NT, typename Proc, typename Rescan>
+template <int NT, int NB, typename Proc, typename Rescan>
 __device__ void run_rounds(int *hdr, uint16_t *Q0, uint16_t *Q1, int qcap, uint16_t *spill, int spill_cap,
                            const int *off, Proc proc, Rescan rescan, unsigned long long deadline, Control *ctl) {
     const int tid = threadIdx.x;
@@ -271,10 +271,14 @@ __device__ void run_rounds(int *hdr, uint16_t *Q0, uint16_t *Q1, int qcap, uint1
         const uint16_t *qg = spill + cur * spill_cap;
         RQ out{cur ? Q0 : Q1, spill + (cur ^ 1) * spill_cap, hdr + H_CNT0 + (cur ^ 1), hdr + H_RESCAN, qcap,
                spill_cap};
-        for (int base = 0; base < n_in; base += NT) {
-            const int i = base + tid;
-            const int p = i < n_in ? rq_get(qs, qg, qcap, i) : -1;
-            const unsigned m = p >= 0 ? proc(p) : 0u;
+        // neighbour-parallel: lane task k handles neighbour k % NB of item
+        // k / NB, so small frontiers still fill the lanes and each lane's
+        // critical path is one neighbour test
+        for (int base = 0; base < n_in * NB; base += NT) {
+            const int k = base + tid;
+            const int item = k / NB, n = k - item * NB;
+            const int p = item < n_in ? rq_get(qs, qg, qcap, item) : -1;
+            const unsigned m = (p >= 0 && proc(p, n)) ? 1u << n : 0u;
             pushed += warp_enqueue(m, p, off, out);
         }
         if (resc) {
@@ -592,22 +596,16 @@ __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t 
     }
     if ((threadIdx.x & 31) == 0) atomicAdd(hdr + H_SEEDS, (int)seeds);
     pc.mark(hdr, 1);
-    auto proc = [&](int p) -> unsigned {
-        const int jp = g.j(p);
+    auto proc = [&](int p, int n) -> bool {
         const int pr = p / G::P, pc = p - pr * G::P - 3;
-        unsigned m = 0;
-#pragma unroll
-        for (int n = 0; n < CONN; ++n) {
-            const int rr = pr + nb_dy(CONN, n), cc = pc + nb_dx(CONN, n);
-            if (rr < 1 || rr > TS || cc < 1 || cc > TS) continue;
-            const int qi = p + off[n];
-            const int v = min(jp, g.iv(qi));
-            if (g.j(qi) < v && g.raise(qi, v)) m |= 1u << n;
-        }
-        return m;
+        const int rr = pr + nb_dy(CONN, n), cc = pc + nb_dx(CONN, n);
+        if (rr < 1 || rr > TS || cc < 1 || cc > TS) return false;
+        const int qi = p + off[n];
+        const int v = min(g.j(p), g.iv(qi));
+        return g.j(qi) < v && g.raise(qi, v);
     };
     auto rescan = [&](const RQ &q) -> unsigned { return g.template dilate<CONN, NT>(q, off); };
-    run_rounds<NT>(hdr, Q0, Q1, QCAP_R, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl);
+    run_rounds<NT, CONN>(hdr, Q0, Q1, QCAP_R, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl);
     pc.mark(hdr, 2);
 }
 
@@ -894,6 +892,128 @@ __device__ __forceinline__ bool edt_try(unsigned *V, int oy, int ox, int pr, int
     }
 }
 
+// Best of the current feature and a candidate for pixel (y, x): the
+// strictly closer one, or the one with smaller packed coordinates when
+// equally close (the same rule as the compare-and-swap updates).
+struct Pick {
+    unsigned best, db;
+    __device__ __forceinline__ Pick(unsigned f, int y, int x) : best(f), db(f == VR_INF ? VR_INF : d2(y, x, f)) {}
+    __device__ __forceinline__ void consider(unsigned cand, int y, int x) {
+        if (cand == VR_INF) return;
+        const unsigned dn = d2(y, x, cand);
+        if (dn < db || (dn == db && cand < best)) {
+            best = cand;
+            db = dn;
+        }
+    }
+};
+
+// Row passes of the distance-transform sweep (one thread per row): each
+// pixel keeps the better of its own feature and its left (then right)
+// neighbour's, as Danielsson's raster vector propagation does.
+__device__ __forceinline__ bool edt_row_passes(unsigned *__restrict__ V, int r, int oy, int ox) {
+    const int base = r * EP + 3, y = oy + r;
+    bool ch = false;
+    unsigned run = V[base];
+#pragma unroll 4
+    for (int c = 1; c <= TS; ++c) {
+        const unsigned f = V[base + c];
+        Pick p(f, y, ox + c);
+        p.consider(run, y, ox + c);
+        if (p.best != f) { V[base + c] = p.best; ch = true; }
+        run = p.best;
+    }
+    run = V[base + TS + 1];
+#pragma unroll 4
+    for (int c = TS; c >= 1; --c) {
+        const unsigned f = V[base + c];
+        Pick p(f, y, ox + c);
+        p.consider(run, y, ox + c);
+        if (p.best != f) { V[base + c] = p.best; ch = true; }
+        run = p.best;
+    }
+    return ch;
+}
+
+// Column pass of the distance-transform sweep (DIR +1 downwards over the
+// upper neighbours, -1 upwards over the lower ones), one thread per column;
+// diagonal neighbours' new features come by warp shuffle, warp-edge lanes
+// read the neighbouring column from shared memory (possibly older: still
+// a valid candidate).
+template <int DIR>
+__device__ __forceinline__ bool edt_column_pass(unsigned *__restrict__ V, int oy, int ox) {
+    const int lane = threadIdx.x & 31;
+    const int c = threadIdx.x + 1, x = ox + c;
+    const int r0 = DIR > 0 ? 0 : RR - 1;
+    unsigned up = V[ecell(r0, c)], ul = V[ecell(r0, c - 1)], ur = V[ecell(r0, c + 1)];
+    bool ch = false;
+#pragma unroll 2
+    for (int s = 1; s <= TS; ++s) {
+        const int r = DIR > 0 ? s : RR - 1 - s;
+        const int i = ecell(r, c), y = oy + r;
+        const unsigned f = V[i];
+        Pick p(f, y, x);
+        p.consider(up, y, x);
+        p.consider(ul, y, x);
+        p.consider(ur, y, x);
+        if (p.best != f) { V[i] = p.best; ch = true; }
+        up = p.best;
+        unsigned nl = __shfl_up_sync(0xffffffffu, up, 1);
+        unsigned nr = __shfl_down_sync(0xffffffffu, up, 1);
+        if (lane == 0) nl = ((volatile unsigned *)V)[i - 1];
+        if (lane == 31) nr = ((volatile unsigned *)V)[i + 1];
+        ul = nl;
+        ur = nr;
+    }
+    return ch;
+}
+
+// One sweep set (rows both ways, columns down and up); block-uniform
+// "changed" result.  A set that changes nothing proves the tile stable.
+__device__ bool edt_sweep_set(unsigned *V, int oy, int ox) {
+    const int t = threadIdx.x;
+    bool ch = false;
+    if (t < TS) ch |= edt_row_passes(V, t + 1, oy, ox);
+    __syncthreads();
+    if (t < TS) {
+        ch |= edt_column_pass<+1>(V, oy, ox);
+        ch |= edt_column_pass<-1>(V, oy, ox);
+    }
+    return __syncthreads_or(ch) != 0;
+}
+
+// One propagation step over the interior: each pixel takes the best feature
+// of its 8-neighbourhood; pixels that change are queued.  Afterwards every
+// pixel that can still improve a neighbour is queued (a pixel that did not
+// change was seen by all its neighbours).  Each pixel is written only by its
+// own thread.
+template <int NT>
+__device__ unsigned edt_dilate_seed(unsigned *V, int oy, int ox, const RQ &q, const int *off) {
+    unsigned pushed = 0;
+    for (int base = 0; base < TS * TS; base += NT) {
+        const int k = base + threadIdx.x;
+        unsigned m = 0;
+        int i = 0;
+        if (k < TS * TS) {
+            const int r = k / TS + 1, c = k - (k / TS) * TS + 1;
+            const int y = oy + r, x = ox + c;
+            i = ecell(r, c);
+            const unsigned f = V[i];
+            if (f != pack_yx(y, x)) {  // features stay
+                Pick p(f, y, x);
+#pragma unroll
+                for (int n = 0; n < 8; ++n) p.consider(V[i + off[n]], y, x);
+                if (p.best != f) {
+                    V[i] = p.best;
+                    m = 1u << 8;
+                }
+            }
+        }
+        pushed += warp_enqueue(m, i, off, q);
+    }
+    return pushed;
+}
+
 template <int NT>
 __device__ unsigned edt_seed_scan(unsigned *V, int oy, int ox, const RQ &q, bool all, const int *off) {
     unsigned pushed = 0;
@@ -996,27 +1116,45 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     pc.mark(hdr, 0);
     const int *off = hdr + H_OFF;
 
-    // 2. seeds: every staged pixel that can improve an interior neighbour on
-    //    a first visit, only the halo on later visits
+    // 2. seeds.  First visit: raster / anti-raster vector-propagation sweeps
+    //    (Danielsson-style, the same rule as the queue updates) until a set
+    //    changes nothing or the set budget is spent, then one propagation
+    //    step whose changed pixels seed the queue.  Later visit: only the
+    //    halo changed; a few entry points seed the queue directly, many
+    //    mean a bulk change handled as on a first visit.
     uint16_t *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
     RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, QCAP_E, ka.spill_cap};
-    const unsigned seeds = edt_seed_scan<NT>(V, oy, ox, q0, first, off);
+    auto sweeps_then_dilate = [&]() -> unsigned {
+        bool changed = true;
+        for (int s = 0; s < ka.edt_sweeps && changed; ++s) changed = edt_sweep_set(V, oy, ox);
+        if (!changed && ka.edt_sweeps > 0) return 0u;
+        return edt_dilate_seed<NT>(V, oy, ox, q0, off);
+    };
+    unsigned seeds;
+    if (first && ka.edt_sweeps > 0) {
+        seeds = sweeps_then_dilate();
+    } else {
+        seeds = edt_seed_scan<NT>(V, oy, ox, q0, first, off);
+        __syncthreads();
+        if (!first && hdr[H_CNT0] > ka.edt_revisit_sweep_min && ka.edt_sweeps > 0) {
+            __syncthreads();
+            if (tid == 0) { hdr[H_CNT0] = 0; hdr[H_RESCAN] = 0; }
+            __syncthreads();
+            seeds = sweeps_then_dilate();
+        }
+    }
     if ((tid & 31) == 0) atomicAdd(hdr + H_SEEDS, (int)seeds);
     pc.mark(hdr, 1);
 
     // 3. propagation rounds
-    auto proc = [&](int p) -> unsigned {
+    auto proc = [&](int p, int n) -> bool {
         const unsigned f = ((volatile unsigned *)V)[p];
-        if (f == VR_INF) return 0u;
+        if (f == VR_INF) return false;
         const int pr = p / EP, pc2 = p - pr * EP - 3;
-        unsigned m = 0;
-#pragma unroll
-        for (int n = 0; n < 8; ++n)
-            if (edt_try(V, oy, ox, pr, pc2, f, n, true)) m |= 1u << n;
-        return m;
+        return edt_try(V, oy, ox, pr, pc2, f, n, true);
     };
     auto rescan = [&](const RQ &q) -> unsigned { return edt_seed_scan<NT>(V, oy, ox, q, true, off); };
-    run_rounds<NT>(hdr, Q0, Q1, QCAP_E, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl);
+    run_rounds<NT, 8>(hdr, Q0, Q1, QCAP_E, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl);
     __syncthreads();
     pc.mark(hdr, 2);
 

@@ -65,6 +65,16 @@ def test_special_cases(cuda_ctx):
     assert sq[0, 0] == 0 and nn[0, 0] == 0
 
 
+@pytest.mark.parametrize("edt_sweeps,revisit", [(0, 0), (1, 0), (2, 0), (1, 64), (3, 1 << 20)])
+def test_sweep_settings_keep_parity(cuda_ctx, edt_sweeps, revisit):
+    # queue-only visits, sweeps on every visit, sweeps on the first visit only:
+    # every setting must satisfy the same parity criterion
+    wl = synth.config_workload("edt4096", size=700)
+    for fnz in (False, True):
+        sq, nn = run(cuda_ctx, wl.binary, fnz, edt_sweeps=edt_sweeps, edt_revisit_sweep_min=revisit)
+        edt_parity(wl.binary, sq, nn, fnz)
+
+
 def test_figure3_fixture(cuda_ctx):
     with open(os.path.join(GOLDEN, "edt_departure_170.json")) as f:
         g = json.load(f)
