@@ -456,7 +456,7 @@ int iwpp_ctx_create(iwpp_ctx **out, int device, size_t hbm_budget_bytes) {
     ctx->budget = hbm_budget_bytes;
     ctx->opt.tile = 0;
     ctx->opt.blocks_per_sm = 0;
-    ctx->opt.sweeps = 2;
+    ctx->opt.sweeps = 3;
     ctx->opt.queue_factor = 32;
     ctx->opt.spill_cap = 8192;
     ctx->opt.max_relaunch = 1;
@@ -759,7 +759,7 @@ int iwpp_plan_autotune(iwpp_plan *p, void *stream, int reps, iwpp_options *best)
     int rc = IWPP_OK;
     const int occ = ctx->occupancy[p->P.fam];
     // sweep candidates per operation; a mixed plan pairs them up
-    const int sweeps_c[3] = {1, 2, 3};
+    const int sweeps_c[3] = {2, 3, 4};
     const int revisit_c[2] = {0, 32};
     const int edt_sweeps_c[3] = {0, 1, 2};
     const int edt_revisit_c[2] = {16, 64};

@@ -378,40 +378,35 @@ __device__ __forceinline__ bool i32_row_passes(int *__restrict__ J, const int *_
 
 // Column pass (N^{0,+} downwards when DIR = +1, N^{0,-} upwards when -1) for
 // the column of this thread: one thread per column, rows in sequence.  The
-// diagonal neighbours' new values of the previous row come by warp shuffle;
-// the warp's edge lanes read the neighbouring column from shared memory,
-// where another warp may not have written it yet -- an older value, which
-// is still a valid lower bound.
+// vertical neighbour is this thread's own running value; the two diagonal
+// neighbours of the previous row are read from shared memory, where the
+// neighbouring columns' threads may or may not have stored their new value
+// yet -- either is a valid lower bound, and keeping the diagonals off the
+// running value's dependency chain leaves two operations per row on it.
+// When a whole sweep set changes nothing, every value read was the current
+// one, so the stability argument is unaffected.
 template <int CONN, int DIR, typename T>
 __device__ __forceinline__ bool column_pass(T *__restrict__ J, const T *__restrict__ I, int P, int c0) {
-    const int lane = threadIdx.x & 31;
     const int c = threadIdx.x + 1;
     const int r0 = DIR > 0 ? 0 : RR - 1;
     int up = J[r0 * P + c0 + c];
-    int ul = CONN == 8 ? J[r0 * P + c0 + c - 1] : 0;
-    int ur = CONN == 8 ? J[r0 * P + c0 + c + 1] : 0;
     bool ch = false;
-#pragma unroll 4
+#pragma unroll 8
     for (int s = 1; s <= TS; ++s) {
         const int r = DIR > 0 ? s : RR - 1 - s;
         const int i = r * P + c0 + c;
         const int o = J[i];
-        int v = max(o, up);
-        if (CONN == 8) v = max(v, max(ul, ur));
-        v = min(v, (int)I[i]);
+        int w = o;
+        if (CONN == 8) {
+            const int ip = i - DIR * P;
+            w = max(w, max((int)J[ip - 1], (int)J[ip + 1]));
+        }
+        const int v = min(max(w, up), (int)I[i]);
         if (v != o) {
             J[i] = (T)v;
             ch = true;
         }
         up = v;
-        if (CONN == 8) {
-            int nl = __shfl_up_sync(0xffffffffu, v, 1);
-            int nr = __shfl_down_sync(0xffffffffu, v, 1);
-            if (lane == 0) nl = ((volatile T *)J)[i - 1];
-            if (lane == 31) nr = ((volatile T *)J)[i + 1];
-            ul = nl;
-            ur = nr;
-        }
     }
     return ch;
 }
@@ -610,28 +605,84 @@ __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t 
 }
 
 // Border test against the neighbours' current values; flags hdr[H_FLAG..].
+// Each thread first issues all its halo loads from global memory, then
+// tests, so the loads' latencies overlap instead of adding up.
 template <typename T, int CONN, int NT, typename G>
 __device__ void recon_border(const JobDesc *jd, const G &g, int *hdr, int x0, int y0) {
+    constexpr int HN = 4 * (TS + 1), HPT = (HN + NT - 1) / NT;
     const T *mk = (const T *)jd->a;
     const T *out = (const T *)jd->out;
-    for (int k = threadIdx.x; k < 4 * (TS + 1); k += NT) {
+    int val[HPT];
+#pragma unroll
+    for (int u = 0; u < HPT; ++u) {
+        const int k = threadIdx.x + u * NT;
+        val[u] = 0;
+        if (k >= HN) continue;
         int r, c;
         halo_cell(k, r, c);
         const int gy = y0 - 1 + r, gx = x0 - 1 + c;
         if (gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w) continue;
         const int reg = region(r) * 3 + region(c);
+        val[u] = hdr[H_SRC + reg] == 1 ? (int)__ldcg(out + (int64_t)gy * jd->po + gx)
+                                       : (int)__ldcg(mk + (int64_t)gy * jd->pa + gx);
+    }
+#pragma unroll
+    for (int u = 0; u < HPT; ++u) {
+        const int k = threadIdx.x + u * NT;
+        if (k >= HN) continue;
+        int r, c;
+        halo_cell(k, r, c);
+        const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+        if (gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w) continue;
         const int i = G::cell(r, c);
         const int iq = g.iv(i);
-        const int v = hdr[H_SRC + reg] == 1 ? (int)__ldcg(out + (int64_t)gy * jd->po + gx)
-                                            : (int)__ldcg(mk + (int64_t)gy * jd->pa + gx);
-        const int jq = min(v, iq);
+        const int jq = min(val[u], iq);
         bool need = false;
 #pragma unroll
         for (int n = 0; n < CONN; ++n) {
             const int pr = r + nb_dy(CONN, n), pc = c + nb_dx(CONN, n);
             if (pr >= 1 && pr <= TS && pc >= 1 && pc <= TS) need |= jq < min(g.j(G::cell(pr, pc)), iq);
         }
-        if (need) hdr[H_FLAG + reg] = 1;
+        if (need) hdr[H_FLAG + region(r) * 3 + region(c)] = 1;
+    }
+}
+
+// Halo cells of neighbour tiles whose J lives in the other buffer (marker
+// vs current result) are read from global memory -- all loads issued before
+// any is used -- then every halo cell is clipped by the mask (halo pixels
+// are sources only, so no later step clips them).
+template <typename T, int NT, typename Cell>
+__device__ __forceinline__ void halo_fixup(const JobDesc *jd, T *J, const T *I, const int *hdr, bool first, int x0,
+                                           int y0, Cell cell) {
+    constexpr int HN = 4 * (TS + 1), HPT = (HN + NT - 1) / NT;
+    const T *mk = (const T *)jd->a;
+    const T *out = (const T *)jd->out;
+    T val[HPT];
+    bool got[HPT];
+#pragma unroll
+    for (int u = 0; u < HPT; ++u) {
+        const int k = threadIdx.x + u * NT;
+        got[u] = false;
+        val[u] = 0;
+        if (k >= HN) continue;
+        int r, c;
+        halo_cell(k, r, c);
+        const int src = hdr[H_SRC + region(r) * 3 + region(c)];
+        const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+        if (src != 2 && src != (first ? 0 : 1) && gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
+            val[u] = src == 1 ? __ldcg(out + (int64_t)gy * jd->po + gx) : __ldcg(mk + (int64_t)gy * jd->pa + gx);
+            got[u] = true;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < HPT; ++u) {
+        const int k = threadIdx.x + u * NT;
+        if (k >= HN) continue;
+        int r, c;
+        halo_cell(k, r, c);
+        const int i = cell(r, c);
+        if (got[u]) J[i] = val[u];
+        if (J[i] > I[i]) J[i] = I[i];
     }
 }
 
@@ -688,23 +739,10 @@ __device__ bool recon_u8_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
         }
     }
     __syncthreads();
-    // halo cells of neighbour tiles whose J lives in the other buffer
-    // (marker vs current result) are read directly; marker values are then
-    // clipped by the mask everywhere no later step does it: the halo ring
-    // always (halo pixels are sources only), the interior on a first visit
-    // without sweeps (the first row pass clips every interior pixel)
-    for (int k = tid; k < 4 * (TS + 1); k += NT) {
-        int r, c;
-        halo_cell(k, r, c);
-        const int i = U8Grid::cell(r, c);
-        const int src = hdr[H_SRC + region(r) * 3 + region(c)];
-        if (src != 2 && src != (first ? 0 : 1)) {
-            const int gy = y0 - 1 + r, gx = x0 - 1 + c;
-            if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w)
-                JW[i] = src == 1 ? __ldcg(out + (int64_t)gy * jd->po + gx) : __ldcg(mk + (int64_t)gy * jd->pa + gx);
-        }
-        if (JW[i] > IW[i]) JW[i] = IW[i];
-    }
+    // halo cells from the other buffer, halo clipped by the mask; the
+    // interior is clipped here on a first visit without sweeps (otherwise
+    // the first row pass clips every interior pixel)
+    halo_fixup<uint8_t, NT>(jd, JW, IW, hdr, first, x0, y0, U8Grid::cell);
     if (first && ka.sweeps == 0)
         for (int k = tid; k < TS * TS; k += NT) {
             const int i = U8Grid::cell(k / TS + 1, k % TS + 1);
@@ -855,18 +893,6 @@ __device__ __forceinline__ bool better(unsigned dn, unsigned f, int qy, int qx, 
 }
 
 __device__ __forceinline__ bool is_feature(uint8_t b, int flags) { return (flags & 1) ? b != 0 : b == 0; }
-
-// current VR of image pixel (gy, gx) read from global memory
-__device__ __forceinline__ unsigned vr_fetch(const JobDesc *jd, bool visited, int gy, int gx) {
-    if (visited) {
-        const int idx = __ldcg(jd->nearest + (int64_t)gy * jd->w + gx);
-        if (idx < 0) return VR_INF;
-        const int fy = idx / jd->w;
-        return pack_yx(fy, idx - fy * jd->w);
-    }
-    const uint8_t b = __ldcg((const uint8_t *)jd->a + (int64_t)gy * jd->pa + gx);
-    return is_feature(b, jd->flags) ? pack_yx(gy, gx) : VR_INF;
-}
 
 constexpr int EP = BI32_W;  // VR row stride (words)
 __device__ __forceinline__ int ecell(int r, int c) { return r * EP + c + 3; }
@@ -1158,44 +1184,85 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     __syncthreads();
     pc.mark(hdr, 2);
 
-    // 4. store nearest (linear index) and squared distance; the
-    //    neighbourhood states for the border test are fetched meanwhile
+    // 4. store nearest (linear index) and squared distance, four pixels per
+    //    16-byte store where rows are 16-byte aligned; the neighbourhood
+    //    states for the border test are fetched meanwhile
     load_sources(ka, jd, tx, ty, hdr);
-    for (int i = tid; i < TS * TS; i += NT) {
-        const int r = i / TS, c = i - r * TS;
-        const int gy = y0 + r, gx = x0 + c;
-        if (gy >= jd->h || gx >= jd->w) continue;
-        const unsigned f = V[ecell(r + 1, c + 1)];
-        const int64_t o = (int64_t)gy * jd->w + gx;
-        if (f == VR_INF) {
-            jd->nearest[o] = -1;
-            jd->sqdist[o] = INT_MAX;
-        } else {
-            jd->nearest[o] = (int)(f >> 16) * jd->w + (int)(f & 0xFFFFu);
-            jd->sqdist[o] = (int)d2(gy, gx, f);
+    {
+        const bool vec = (jd->w & 3) == 0 && ((reinterpret_cast<uintptr_t>(jd->nearest) |
+                                                reinterpret_cast<uintptr_t>(jd->sqdist)) & 15) == 0;
+        for (int i = tid; i < TS * TS / 4; i += NT) {
+            const int r = i >> 4, q = i & 15;
+            const int gy = y0 + r, gx = x0 + 4 * q;
+            if (gy >= jd->h || gx >= jd->w) continue;
+            int nv[4], dv[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const unsigned f = V[ecell(r + 1, 4 * q + b + 1)];
+                nv[b] = f == VR_INF ? -1 : (int)(f >> 16) * jd->w + (int)(f & 0xFFFFu);
+                dv[b] = f == VR_INF ? INT_MAX : (int)d2(gy, gx + b, f);
+            }
+            const int64_t o = (int64_t)gy * jd->w + gx;
+            if (vec && gx + 4 <= jd->w) {
+                *(int4 *)(jd->nearest + o) = make_int4(nv[0], nv[1], nv[2], nv[3]);
+                *(int4 *)(jd->sqdist + o) = make_int4(dv[0], dv[1], dv[2], dv[3]);
+            } else {
+                for (int b = 0; b < 4 && gx + b < jd->w; ++b) {
+                    jd->nearest[o + b] = nv[b];
+                    jd->sqdist[o + b] = dv[b];
+                }
+            }
         }
     }
     __syncthreads();
     publish_tile(ka, gt, hdr);
 
-    // 5. border test (strict distance rule across tiles)
-    for (int k = tid; k < 4 * (TS + 1); k += NT) {
-        int r, c;
-        halo_cell(k, r, c);
-        const int gy = oy + r, gx = ox + c;
-        if (gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w) continue;
-        const int reg = region(r) * 3 + region(c);
-        const unsigned cq = vr_fetch(jd, hdr[H_SRC + reg] == 1, gy, gx);
-        const unsigned dq = cq == VR_INF ? VR_INF : d2(gy, gx, cq);
-        bool need = false;
+    // 5. border test (strict distance rule across tiles); every halo load
+    //    is issued before any is used
+    {
+        constexpr int HN = 4 * (TS + 1), HPT = (HN + NT - 1) / NT;
+        int raw[HPT];
 #pragma unroll
-        for (int n = 0; n < 8; ++n) {
-            const int pr = r + nb_dy(8, n), pcc = c + nb_dx(8, n);
-            if (pr < 1 || pr > TS || pcc < 1 || pcc > TS) continue;
-            const unsigned fp = V[ecell(pr, pcc)];
-            if (fp != VR_INF && d2(gy, gx, fp) < dq) need = true;
+        for (int u = 0; u < HPT; ++u) {
+            const int k = tid + u * NT;
+            raw[u] = 0;
+            if (k >= HN) continue;
+            int r, c;
+            halo_cell(k, r, c);
+            const int gy = oy + r, gx = ox + c;
+            if (gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w) continue;
+            raw[u] = hdr[H_SRC + region(r) * 3 + region(c)] == 1
+                         ? __ldcg(jd->nearest + (int64_t)gy * jd->w + gx)
+                         : (int)__ldcg((const uint8_t *)jd->a + (int64_t)gy * jd->pa + gx);
         }
-        if (need) hdr[H_FLAG + reg] = 1;
+#pragma unroll
+        for (int u = 0; u < HPT; ++u) {
+            const int k = tid + u * NT;
+            if (k >= HN) continue;
+            int r, c;
+            halo_cell(k, r, c);
+            const int gy = oy + r, gx = ox + c;
+            if (gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w) continue;
+            const int reg = region(r) * 3 + region(c);
+            unsigned cq;
+            if (hdr[H_SRC + reg] == 1) {
+                const int idx = raw[u];
+                const int fy = idx / jd->w;
+                cq = idx < 0 ? (unsigned)VR_INF : pack_yx(fy, idx - fy * jd->w);
+            } else {
+                cq = is_feature((uint8_t)raw[u], jd->flags) ? pack_yx(gy, gx) : (unsigned)VR_INF;
+            }
+            const unsigned dq = cq == VR_INF ? (unsigned)VR_INF : d2(gy, gx, cq);
+            bool need = false;
+#pragma unroll
+            for (int n = 0; n < 8; ++n) {
+                const int pr = r + nb_dy(8, n), pcc = c + nb_dx(8, n);
+                if (pr < 1 || pr > TS || pcc < 1 || pcc > TS) continue;
+                const unsigned fp = V[ecell(pr, pcc)];
+                if (fp != VR_INF && d2(gy, gx, fp) < dq) need = true;
+            }
+            if (need) hdr[H_FLAG + reg] = 1;
+        }
     }
     __syncthreads();
     finish_tile(ka, jd, gt, tx, ty, hdr);
