@@ -44,18 +44,18 @@ namespace iwpp {
 
 constexpr int TS = TILE;       // 64
 constexpr int RR = TS + 2;     // staged rows / columns
-constexpr int QCAP_R = 2048;   // reconstruction block-queue entries per buffer
+constexpr int QCAP_R = 2048;   // int32 reconstruction block-queue entries per buffer
+constexpr int QCAP_U8 = 512;   // uint8 reconstruction block-queue entries per buffer
 constexpr int QCAP_E = 2048;   // distance-transform block-queue entries per buffer
 
 // u8 TMA box: columns x0-16 .. x0+79 (96), rows y0-1 .. y0+64 (66)
 constexpr int BU8_W = 96, BU8_BYTES = BU8_W * RR, BU8_PAD = 6400;
 // int32 TMA box: columns x0-4 .. x0+67 (72), rows y0-1 .. y0+64
 constexpr int BI32_W = 72, BI32_BYTES = BI32_W * RR * 4, BI32_PAD = 19072;
-// u8 working layout: row stride 76 bytes (19 words: an odd word stride keeps
-// one-row-per-thread walks free of bank conflicts); cell (r, c) at byte
-// r*76 + c + 3, so that word k of a row holds cells 4k-3 .. 4k and box word
-// k+3 maps onto working word k.
-constexpr int WU8_P = 76, WU8_PAD = 5120;
+// u8 working layout = the u8 TMA box: row stride 96 bytes, cell (r, c) at
+// byte r*96 + c + 15, so the 64 interior cells of a row are four aligned
+// 16-byte words (bytes 16 .. 79).
+constexpr int WU8_P = BU8_W, WU8_C0 = 15;
 // distance-transform working array: the int32 TMA box layout (stride 72,
 // cell (r, c) at word r*72 + c + 3), holding packed feature coordinates
 
@@ -70,17 +70,20 @@ enum : int {
 };
 constexpr int HDR_BYTES = 512;  // header ints + mbarrier at byte 256
 
-// byte offsets of the layouts
-constexpr int RU8_JW = HDR_BYTES, RU8_IW = RU8_JW + WU8_PAD, RU8_U = RU8_IW + WU8_PAD;
-constexpr int RU8_BYTES = RU8_U + 2 * BU8_PAD;
+// byte offsets of the layouts.  The uint8 reconstruction works in its two
+// TMA boxes and keeps short block queues (overflow spills to global): its
+// visits are latency-bound, so shared memory per CTA -- which sets the
+// resident CTAs per SM -- is what its throughput follows.
+constexpr int RU8_JW = HDR_BYTES, RU8_IW = RU8_JW + BU8_PAD, RU8_U = RU8_IW + BU8_PAD;
+constexpr int RU8_BYTES = RU8_U + 2 * QCAP_U8 * 2;
 constexpr int RI32_J = HDR_BYTES, RI32_I = RI32_J + BI32_PAD, RI32_U = RI32_I + BI32_PAD;
 constexpr int RI32_BYTES = RI32_U + BI32_PAD;
 constexpr int E_W = HDR_BYTES, E_U = E_W + BI32_PAD;
 constexpr int E_BYTES = E_U + 2 * QCAP_E * 2;
-static_assert(RU8_U % 128 == 0 && RI32_J % 128 == 0 && RI32_I % 128 == 0 && RI32_U % 128 == 0 &&
+static_assert(RU8_JW % 128 == 0 && RU8_IW % 128 == 0 && RI32_J % 128 == 0 && RI32_I % 128 == 0 && RI32_U % 128 == 0 &&
                   E_U % 128 == 0 && E_W % 128 == 0,
               "TMA destinations must be 128-byte aligned");
-static_assert(2 * QCAP_R * 2 <= 2 * BU8_PAD && 2 * QCAP_R * 2 <= BI32_PAD &&
+static_assert(2 * QCAP_R * 2 <= BI32_PAD &&
                   BU8_PAD <= 2 * QCAP_E * 2,
               "queues must fit the staging union");
 
@@ -88,6 +91,9 @@ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int FAM_SMEM[FAM_COUNT] = {RU8_BYTES, RI32_BYTES, E_BYTES,
                                      cmax(cmax(RU8_BYTES, RI32_BYTES), E_BYTES)};
 constexpr int FAM_NT[FAM_COUNT] = {64, 64, 128, 128};
+// resident CTAs per SM that each family's shared memory allows; the
+// register budget is sized for them
+constexpr int FAM_MINB[FAM_COUNT] = {14, 3, 8, 3};
 
 // neighbourhood offsets (dy, dx); 8-connected: the first 4 are N+ (raster)
 __device__ __forceinline__ int nb_dy(int conn, int k) {
@@ -332,28 +338,53 @@ __device__ __forceinline__ bool wait_boxes(uint64_t *bar, uint32_t &phase, unsig
 // =====================================================================
 
 // Row passes (N^{+,0} left to right, then N^{-,0} right to left) of one
-// uint8 working row; one thread owns the row during the pass, so plain
-// loads can run ahead of the running value.
+// uint8 working row, owned by one thread.  The 64 interior cells of J and I
+// come as four 16-byte shared loads each and are worked on in registers,
+// bytes extracted and re-inserted; the running value's dependency chain is
+// one max and one min per cell.
 __device__ __forceinline__ bool u8_row_passes(uint8_t *__restrict__ J, const uint8_t *__restrict__ I, int r) {
-    const int base = r * WU8_P + 3;
-    bool ch = false;
+    const int base = r * WU8_P + WU8_C0;  // cell 0
+    uint4 *jp = (uint4 *)(J + base + 1);   // cells 1 .. 64
+    const uint4 *ip = (const uint4 *)(I + base + 1);
+    uint32_t j[16], m[16];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint4 a = jp[k], b = ip[k];
+        j[4 * k] = a.x; j[4 * k + 1] = a.y; j[4 * k + 2] = a.z; j[4 * k + 3] = a.w;
+        m[4 * k] = b.x; m[4 * k + 1] = b.y; m[4 * k + 2] = b.z; m[4 * k + 3] = b.w;
+    }
+    uint32_t diff = 0;
     int run = J[base];
-#pragma unroll 8
-    for (int c = 1; c <= TS; ++c) {
-        const int o = J[base + c];
-        const int v = min((int)I[base + c], max(o, run));
-        if (v != o) { J[base + c] = (uint8_t)v; ch = true; }
-        run = v;
+#pragma unroll
+    for (int w = 0; w < 16; ++w) {
+        uint32_t nw = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            run = min((int)((m[w] >> (8 * b)) & 0xFFu), max((int)((j[w] >> (8 * b)) & 0xFFu), run));
+            nw |= (uint32_t)run << (8 * b);
+        }
+        diff |= nw ^ j[w];
+        j[w] = nw;
     }
+    // (the second pass extracts with byte permutes, which keeps the compiler
+    // from holding all 64 mask bytes live across the two passes)
     run = J[base + TS + 1];
-#pragma unroll 8
-    for (int c = TS; c >= 1; --c) {
-        const int o = J[base + c];
-        const int v = min((int)I[base + c], max(o, run));
-        if (v != o) { J[base + c] = (uint8_t)v; ch = true; }
-        run = v;
+#pragma unroll
+    for (int w = 15; w >= 0; --w) {
+        uint32_t nw = 0;
+#pragma unroll
+        for (int b = 3; b >= 0; --b) {
+            run = min((int)__byte_perm(m[w], 0u, 0x4440u | b), max((int)__byte_perm(j[w], 0u, 0x4440u | b), run));
+            nw |= (uint32_t)run << (8 * b);
+        }
+        diff |= nw ^ j[w];
+        j[w] = nw;
     }
-    return ch;
+    if (diff) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) jp[k] = make_uint4(j[4 * k], j[4 * k + 1], j[4 * k + 2], j[4 * k + 3]);
+    }
+    return diff != 0;
 }
 
 // Row passes for int32 rows (one thread per row).
@@ -422,8 +453,8 @@ __device__ bool sweep_set_u8(uint8_t *J, const uint8_t *I) {
     if (t < TS) ch |= u8_row_passes(J, I, t + 1);
     __syncthreads();
     if (t < TS) {
-        ch |= column_pass<CONN, +1>(J, I, WU8_P, 3);
-        ch |= column_pass<CONN, -1>(J, I, WU8_P, 3);
+        ch |= column_pass<CONN, +1>(J, I, WU8_P, WU8_C0);
+        ch |= column_pass<CONN, -1>(J, I, WU8_P, WU8_C0);
     }
     return __syncthreads_or(ch) != 0;
 }
@@ -480,11 +511,11 @@ __device__ unsigned dilate_seed(T *__restrict__ J, const T *__restrict__ I, int 
 }
 
 // Access policy for the two value layouts.
-struct U8Grid {  // uint8 images: working copy, stride 76 bytes
+struct U8Grid {  // uint8 images: the TMA box layout, stride 96 bytes
     uint8_t *J;
     const uint8_t *I;
-    static constexpr int P = WU8_P;
-    static __device__ __forceinline__ int cell(int r, int c) { return r * P + c + 3; }
+    static constexpr int P = WU8_P, C0 = WU8_C0, QCAP = QCAP_U8;
+    static __device__ __forceinline__ int cell(int r, int c) { return r * P + c + C0; }
     __device__ __forceinline__ int j(int i) const { return ((volatile uint8_t *)J)[i]; }
     __device__ __forceinline__ int iv(int i) const { return I[i]; }
     __device__ __forceinline__ void set(int i, int v) const { ((volatile uint8_t *)J)[i] = (uint8_t)v; }
@@ -506,15 +537,15 @@ struct U8Grid {  // uint8 images: working copy, stride 76 bytes
     }
     template <int CONN, int NT>
     __device__ __forceinline__ unsigned dilate(const RQ &q, const int *off) const {
-        return dilate_seed<CONN, NT, uint8_t>(J, I, P, 3, q, off);
+        return dilate_seed<CONN, NT, uint8_t>(J, I, P, C0, q, off);
     }
 };
 
 struct I32Grid {  // int32 images: TMA box layout, stride 72 words
     int *J;
     const int *I;
-    static constexpr int P = BI32_W;
-    static __device__ __forceinline__ int cell(int r, int c) { return r * P + c + 3; }
+    static constexpr int P = BI32_W, C0 = 3, QCAP = QCAP_R;
+    static __device__ __forceinline__ int cell(int r, int c) { return r * P + c + C0; }
     __device__ __forceinline__ int j(int i) const { return ((volatile int *)J)[i]; }
     __device__ __forceinline__ int iv(int i) const { return I[i]; }
     __device__ __forceinline__ void set(int i, int v) const { ((volatile int *)J)[i] = v; }
@@ -530,7 +561,7 @@ struct I32Grid {  // int32 images: TMA box layout, stride 72 words
 
 template <typename G>
 __device__ __forceinline__ bool interior(int i) {
-    const int r = i / G::P, c = i - r * G::P - 3;
+    const int r = i / G::P, c = i - r * G::P - G::C0;
     return r >= 1 && r <= TS && c >= 1 && c <= TS;
 }
 
@@ -565,7 +596,7 @@ template <int CONN, int NT, typename G>
 __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t *Q0, uint16_t *Q1, bool first,
                                 const int *off, PhaseClock &pc, unsigned long long deadline) {
     uint16_t *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
-    RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, QCAP_R, ka.spill_cap};
+    RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, G::QCAP, ka.spill_cap};
     auto sweeps_then_dilate = [&](const RQ &q) -> unsigned {
         bool changed = true;
         for (int s = 0; s < ka.sweeps && changed; ++s) changed = g.sweep(CONN);
@@ -592,7 +623,7 @@ __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t 
     if ((threadIdx.x & 31) == 0) atomicAdd(hdr + H_SEEDS, (int)seeds);
     pc.mark(hdr, 1);
     auto proc = [&](int p, int n) -> bool {
-        const int pr = p / G::P, pc = p - pr * G::P - 3;
+        const int pr = p / G::P, pc = p - pr * G::P - G::C0;
         const int rr = pr + nb_dy(CONN, n), cc = pc + nb_dx(CONN, n);
         if (rr < 1 || rr > TS || cc < 1 || cc > TS) return false;
         const int qi = p + off[n];
@@ -600,7 +631,7 @@ __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t 
         return g.j(qi) < v && g.raise(qi, v);
     };
     auto rescan = [&](const RQ &q) -> unsigned { return g.template dilate<CONN, NT>(q, off); };
-    run_rounds<NT, CONN>(hdr, Q0, Q1, QCAP_R, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl);
+    run_rounds<NT, CONN>(hdr, Q0, Q1, G::QCAP, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl);
     pc.mark(hdr, 2);
 }
 
@@ -693,9 +724,7 @@ __device__ bool recon_u8_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
     uint64_t *bar = (uint64_t *)(sm + 256);
     uint8_t *JW = (uint8_t *)(sm + RU8_JW);
     uint8_t *IW = (uint8_t *)(sm + RU8_IW);
-    uint8_t *IB = (uint8_t *)(sm + RU8_U);
-    uint8_t *JB = IB + BU8_PAD;  // the tile's own J source (marker or current result)
-    uint16_t *Q0 = (uint16_t *)(sm + RU8_U), *Q1 = Q0 + QCAP_R;
+    uint16_t *Q0 = (uint16_t *)(sm + RU8_U), *Q1 = Q0 + QCAP_U8;
     const int tid = threadIdx.x;
     const int lt = gt - jd->tile_base, tx = lt % jd->tiles_x, ty = lt / jd->tiles_x;
     const int x0 = tx * TS, y0 = ty * TS;
@@ -712,33 +741,23 @@ __device__ bool recon_u8_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
     const uint8_t *jsrc = first ? mk : out;
     const int64_t jpitch = first ? jd->pa : jd->po;
 
-    // 1. stage the mask box and the box of the tile's own J source
+    // 1. stage the mask box and the box of the tile's own J source (marker
+    //    on a first visit, the current result later); the boxes are the
+    //    working layout.  Cells outside the image are zero in J and I (zero
+    //    fill) and so never raise or get raised.
     if (jd->use_tma) {
         if (tid == 0) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, 2 * BU8_BYTES);
-            tma_load_2d(IB, &jd->tm[1], x0 - 16, y0 - 1, bar);
-            tma_load_2d(JB, &jd->tm[first ? 0 : 2], x0 - 16, y0 - 1, bar);
+            tma_load_2d(IW, &jd->tm[1], x0 - 16, y0 - 1, bar);
+            tma_load_2d(JW, &jd->tm[first ? 0 : 2], x0 - 16, y0 - 1, bar);
         }
         if (!wait_boxes(bar, phase, deadline, ka.ctl)) return false;
     } else {
-        stage_plain<uint8_t, BU8_W>(IB, ms, jd->pb, jd->h, jd->w, x0 - 16, y0 - 1, NT);
-        stage_plain<uint8_t, BU8_W>(JB, jsrc, jpitch, jd->h, jd->w, x0 - 16, y0 - 1, NT);
+        stage_plain<uint8_t, BU8_W>(IW, ms, jd->pb, jd->h, jd->w, x0 - 16, y0 - 1, NT);
+        stage_plain<uint8_t, BU8_W>(JW, jsrc, jpitch, jd->h, jd->w, x0 - 16, y0 - 1, NT);
         __syncthreads();
     }
-    // working copy (word copies; word 18 of a row is padding).  Cells
-    // outside the image are zero in J and I (zero fill) and so never raise
-    // or get raised.
-    {
-        const uint32_t *I32 = (const uint32_t *)IB, *J32 = (const uint32_t *)JB;
-        uint32_t *JW32 = (uint32_t *)JW, *IW32 = (uint32_t *)IW;
-        for (int i = tid; i < RR * 19; i += NT) {
-            const int r = i / 19, k = i - r * 19;
-            IW32[i] = k == 18 ? 0u : I32[r * 24 + 3 + k];
-            JW32[i] = k == 18 ? 0u : J32[r * 24 + 3 + k];
-        }
-    }
-    __syncthreads();
     // halo cells from the other buffer, halo clipped by the mask; the
     // interior is clipped here on a first visit without sweeps (otherwise
     // the first row pass clips every interior pixel)
@@ -767,13 +786,13 @@ __device__ bool recon_u8_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
             const int r = i >> 2, q = i & 3;
             const int gy = y0 + r, gx = x0 + q * 16;
             if (gy >= jd->h || gx >= jd->w) continue;
-            const uint32_t *src = (const uint32_t *)(JW + (r + 1) * WU8_P + 4 + q * 16);
+            const uint32_t *src = (const uint32_t *)(JW + (r + 1) * WU8_P + WU8_C0 + 1 + q * 16);
             uint8_t *dst = out + (int64_t)gy * jd->po + gx;
             if (vec && gx + 16 <= jd->w) {
                 *(uint4 *)dst = make_uint4(src[0], src[1], src[2], src[3]);
             } else {
                 const int n = min(16, jd->w - gx);
-                for (int b = 0; b < n; ++b) dst[b] = JW[(r + 1) * WU8_P + 4 + q * 16 + b];
+                for (int b = 0; b < n; ++b) dst[b] = JW[(r + 1) * WU8_P + WU8_C0 + 1 + q * 16 + b];
             }
         }
     }
@@ -1275,7 +1294,7 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
 // =====================================================================
 
 template <int FAM>
-__global__ void __launch_bounds__(FAM_NT[FAM]) persistent_kernel(const __grid_constant__ KArgs ka) {
+__global__ void __launch_bounds__(FAM_NT[FAM], FAM_MINB[FAM]) persistent_kernel(const __grid_constant__ KArgs ka) {
     constexpr int NT = FAM_NT[FAM];
     extern __shared__ __align__(128) char smem[];
     int *hdr = (int *)smem;
