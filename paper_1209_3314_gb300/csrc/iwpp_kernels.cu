@@ -339,52 +339,41 @@ __device__ __forceinline__ bool wait_boxes(uint64_t *bar, uint32_t &phase, unsig
 
 // Row passes (N^{+,0} left to right, then N^{-,0} right to left) of one
 // uint8 working row, owned by one thread.  The 64 interior cells of J and I
-// come as four 16-byte shared loads each and are worked on in registers,
-// bytes extracted and re-inserted; the running value's dependency chain is
-// one max and one min per cell.
-__device__ __forceinline__ bool u8_row_passes(uint8_t *__restrict__ J, const uint8_t *__restrict__ I, int r) {
-    const int base = r * WU8_P + WU8_C0;  // cell 0
-    uint4 *jp = (uint4 *)(J + base + 1);   // cells 1 .. 64
+// are handled as four 16-byte chunks: each chunk comes with one shared load
+// per image, its 16 cells are worked on in registers (bytes extracted and
+// re-inserted) and it is stored back only if it changed.  The running
+// value's dependency chain is one max and one min per cell; the chunk loop
+// stays rolled to keep the kernel's instruction footprint small.
+template <int DIR>
+__device__ __forceinline__ bool u8_row_pass(uint8_t *__restrict__ J, const uint8_t *__restrict__ I, int base) {
+    uint4 *jp = (uint4 *)(J + base + 1);  // cells 1 .. 64
     const uint4 *ip = (const uint4 *)(I + base + 1);
-    uint32_t j[16], m[16];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint4 a = jp[k], b = ip[k];
-        j[4 * k] = a.x; j[4 * k + 1] = a.y; j[4 * k + 2] = a.z; j[4 * k + 3] = a.w;
-        m[4 * k] = b.x; m[4 * k + 1] = b.y; m[4 * k + 2] = b.z; m[4 * k + 3] = b.w;
-    }
+    int run = J[base + (DIR > 0 ? 0 : TS + 1)];
     uint32_t diff = 0;
-    int run = J[base];
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) {
+        const int k = DIR > 0 ? s : 3 - s;
+        const uint4 a = jp[k], bm = ip[k];
+        const uint32_t j[4] = {a.x, a.y, a.z, a.w}, m[4] = {bm.x, bm.y, bm.z, bm.w};
+        uint32_t nw[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-    for (int w = 0; w < 16; ++w) {
-        uint32_t nw = 0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int q = 0; q < 16; ++q) {
+            const int c = DIR > 0 ? q : 15 - q, w = c >> 2, b = c & 3;
             run = min((int)((m[w] >> (8 * b)) & 0xFFu), max((int)((j[w] >> (8 * b)) & 0xFFu), run));
-            nw |= (uint32_t)run << (8 * b);
+            nw[w] |= (uint32_t)run << (8 * b);
         }
-        diff |= nw ^ j[w];
-        j[w] = nw;
-    }
-    // (the second pass extracts with byte permutes, which keeps the compiler
-    // from holding all 64 mask bytes live across the two passes)
-    run = J[base + TS + 1];
-#pragma unroll
-    for (int w = 15; w >= 0; --w) {
-        uint32_t nw = 0;
-#pragma unroll
-        for (int b = 3; b >= 0; --b) {
-            run = min((int)__byte_perm(m[w], 0u, 0x4440u | b), max((int)__byte_perm(j[w], 0u, 0x4440u | b), run));
-            nw |= (uint32_t)run << (8 * b);
-        }
-        diff |= nw ^ j[w];
-        j[w] = nw;
-    }
-    if (diff) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) jp[k] = make_uint4(j[4 * k], j[4 * k + 1], j[4 * k + 2], j[4 * k + 3]);
+        const uint32_t d = (nw[0] ^ j[0]) | (nw[1] ^ j[1]) | (nw[2] ^ j[2]) | (nw[3] ^ j[3]);
+        if (d) jp[k] = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+        diff |= d;
     }
     return diff != 0;
+}
+
+__device__ __forceinline__ bool u8_row_passes(uint8_t *__restrict__ J, const uint8_t *__restrict__ I, int r) {
+    const int base = r * WU8_P + WU8_C0;  // cell 0
+    const bool a = u8_row_pass<+1>(J, I, base);
+    const bool b = u8_row_pass<-1>(J, I, base);
+    return a || b;
 }
 
 // Row passes for int32 rows (one thread per row).
@@ -422,7 +411,7 @@ __device__ __forceinline__ bool column_pass(T *__restrict__ J, const T *__restri
     const int r0 = DIR > 0 ? 0 : RR - 1;
     int up = J[r0 * P + c0 + c];
     bool ch = false;
-#pragma unroll 8
+#pragma unroll 4
     for (int s = 1; s <= TS; ++s) {
         const int r = DIR > 0 ? s : RR - 1 - s;
         const int i = r * P + c0 + c;
