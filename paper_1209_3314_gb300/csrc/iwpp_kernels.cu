@@ -68,7 +68,8 @@ enum : int {
     H_OFF = 32,   // 9 neighbour offsets of the current layout
     H_PH = 48,    // 4 phase durations of the visit (ns, low 32 bits)
 };
-constexpr int HDR_BYTES = 512;  // header ints + mbarrier at byte 256
+constexpr int HDR_BYTES = 512;  // header ints, mbarrier at byte 256, CTA counters at byte 320
+constexpr int HDR_STATS = 320;  // 10 x u64: tiles, seeds, pushes, spills, rescans, rounds, phase[4]
 
 // byte offsets of the layouts.  The uint8 reconstruction works in its two
 // TMA boxes and keeps short block queues (overflow spills to global): its
@@ -155,18 +156,21 @@ __device__ __forceinline__ void publish_tile(const KArgs &ka, int gt, int *hdr) 
     }
 }
 
-// Queues the flagged neighbours (threads 0..8, one neighbour each, in
-// parallel) and ends the visit.  Called by all threads after the border
-// test; the pushes precede the caller's pending-count decrement.
+// Queues the flagged neighbours (threads 0..8, one neighbour each) and, in
+// parallel on thread 4, ends the tile's own visit (tq_finish: a fence, then
+// the state change, which re-queues the tile if a neighbour asked
+// meanwhile).  Called by all threads after the border test; the barrier at
+// the end precedes the caller's fenced pending-count decrement, so every
+// push is performed before it.
 __device__ __forceinline__ void finish_tile(const KArgs &ka, const JobDesc *jd, int gt, int tx, int ty, int *hdr) {
     const int k = threadIdx.x;
-    if (k < 9 && k != 4 && hdr[H_FLAG + k]) {
+    if (k == 4) {
+        tq_finish(ka.tq, ka.ctl, gt);
+    } else if (k < 9 && hdr[H_FLAG + k]) {
         __threadfence();
         tq_push(ka.tq, ka.ctl, jd->tile_base + (ty + k / 3 - 1) * jd->tiles_x + tx + k % 3 - 1);
-        __threadfence();  // the push is performed before the caller's pending decrement
     }
     __syncthreads();
-    if (k == 0) tq_finish(ka.tq, ka.ctl, gt);
 }
 
 // Per-visit phase timing (thread 0): mark(i) closes phase i.
@@ -1289,7 +1293,9 @@ __global__ void __launch_bounds__(FAM_NT[FAM], FAM_MINB[FAM]) persistent_kernel(
     int *hdr = (int *)smem;
     uint64_t *bar = (uint64_t *)(smem + 256);
     if (ld_volatile(&ka.ctl->done)) return;
+    unsigned long long *cst = (unsigned long long *)(smem + HDR_STATS);
     if (threadIdx.x == 0) mbar_init(bar, 1);
+    if (threadIdx.x < 10) cst[threadIdx.x] = 0;
     __syncthreads();
     uint32_t phase = 0;
     const unsigned long long deadline = globaltimer_ns() + ka.timeout_ns;
@@ -1324,22 +1330,32 @@ __global__ void __launch_bounds__(FAM_NT[FAM], FAM_MINB[FAM]) persistent_kernel(
         }
         if (!ok) break;  // timeout raised; the host reports it
         if (threadIdx.x == 0) {
-            t_visit += globaltimer_ns() - t0;
-            atomicAdd(&ka.ctl->tiles_processed, 1ull);
-            atomicAdd(&ka.ctl->seeds, (unsigned long long)hdr[H_SEEDS]);
-            atomicAdd(&ka.ctl->pushes, (unsigned long long)hdr[H_PUSH]);
-            atomicAdd(&ka.ctl->spills, (unsigned long long)hdr[H_SPILL]);
-            atomicAdd(&ka.ctl->rescans, (unsigned long long)hdr[H_RESC]);
-            atomicAdd(&ka.ctl->rounds, (unsigned long long)hdr[H_ROUNDS]);
-            for (int i = 0; i < 4; ++i) atomicAdd(&ka.ctl->phase_ns[i], (unsigned long long)(unsigned)hdr[H_PH + i]);
+            // the visit's pushes (ordered before by finish_tile's barrier)
+            // are performed before its pending count goes
             __threadfence();
             atomicSub(ka.tq.pending, 1);
+            t_visit += globaltimer_ns() - t0;
+            // per-visit counters accumulate in shared memory; one flush per CTA
+            cst[0] += 1;
+            cst[1] += (unsigned)hdr[H_SEEDS];
+            cst[2] += (unsigned)hdr[H_PUSH];
+            cst[3] += (unsigned)hdr[H_SPILL];
+            cst[4] += (unsigned)hdr[H_RESC];
+            cst[5] += (unsigned)hdr[H_ROUNDS];
+            for (int i = 0; i < 4; ++i) cst[6 + i] += (unsigned)hdr[H_PH + i];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         atomicAdd(&ka.ctl->wait_ns, t_wait);
         atomicAdd(&ka.ctl->visit_ns, t_visit);
+        atomicAdd(&ka.ctl->tiles_processed, cst[0]);
+        atomicAdd(&ka.ctl->seeds, cst[1]);
+        atomicAdd(&ka.ctl->pushes, cst[2]);
+        atomicAdd(&ka.ctl->spills, cst[3]);
+        atomicAdd(&ka.ctl->rescans, cst[4]);
+        atomicAdd(&ka.ctl->rounds, cst[5]);
+        for (int i = 0; i < 4; ++i) atomicAdd(&ka.ctl->phase_ns[i], cst[6 + i]);
     }
 }
 
