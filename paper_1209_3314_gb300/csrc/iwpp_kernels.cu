@@ -974,34 +974,29 @@ __device__ __forceinline__ bool edt_row_passes(unsigned *__restrict__ V, int r, 
 }
 
 // Column pass of the distance-transform sweep (DIR +1 downwards over the
-// upper neighbours, -1 upwards over the lower ones), one thread per column;
-// diagonal neighbours' new features come by warp shuffle, warp-edge lanes
-// read the neighbouring column from shared memory (possibly older: still
-// a valid candidate).
+// upper neighbours, -1 upwards over the lower ones), one thread per column.
+// The vertical candidate is this thread's running feature; the diagonal
+// ones are read from shared memory, where the neighbouring columns' threads
+// may or may not have stored their new feature yet -- either is a valid
+// candidate, and keeping them off the running feature's dependency chain
+// leaves only the vertical candidate's test on it.
 template <int DIR>
 __device__ __forceinline__ bool edt_column_pass(unsigned *__restrict__ V, int oy, int ox) {
-    const int lane = threadIdx.x & 31;
     const int c = threadIdx.x + 1, x = ox + c;
     const int r0 = DIR > 0 ? 0 : RR - 1;
-    unsigned up = V[ecell(r0, c)], ul = V[ecell(r0, c - 1)], ur = V[ecell(r0, c + 1)];
+    unsigned up = V[ecell(r0, c)];
     bool ch = false;
 #pragma unroll 2
     for (int s = 1; s <= TS; ++s) {
         const int r = DIR > 0 ? s : RR - 1 - s;
-        const int i = ecell(r, c), y = oy + r;
+        const int i = ecell(r, c), y = oy + r, ip = i - DIR * EP;
         const unsigned f = V[i];
         Pick p(f, y, x);
+        p.consider(V[ip - 1], y, x);
+        p.consider(V[ip + 1], y, x);
         p.consider(up, y, x);
-        p.consider(ul, y, x);
-        p.consider(ur, y, x);
         if (p.best != f) { V[i] = p.best; ch = true; }
         up = p.best;
-        unsigned nl = __shfl_up_sync(0xffffffffu, up, 1);
-        unsigned nr = __shfl_down_sync(0xffffffffu, up, 1);
-        if (lane == 0) nl = ((volatile unsigned *)V)[i - 1];
-        if (lane == 31) nr = ((volatile unsigned *)V)[i + 1];
-        ul = nl;
-        ur = nr;
     }
     return ch;
 }
