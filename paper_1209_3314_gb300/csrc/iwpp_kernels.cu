@@ -44,7 +44,7 @@ namespace iwpp {
 
 constexpr int TS = TILE;       // 64
 constexpr int RR = TS + 2;     // staged rows / columns
-constexpr int QCAP_R = 2048;   // int32 reconstruction block-queue entries per buffer
+constexpr int QCAP_R = 1024;   // int32 reconstruction block-queue entries per buffer
 constexpr int QCAP_U8 = 512;   // uint8 reconstruction block-queue entries per buffer
 constexpr int QCAP_E = 2048;   // distance-transform block-queue entries per buffer
 
@@ -78,13 +78,13 @@ constexpr int HDR_STATS = 320;  // 10 x u64: tiles, seeds, pushes, spills, resca
 constexpr int RU8_JW = HDR_BYTES, RU8_IW = RU8_JW + BU8_PAD, RU8_U = RU8_IW + BU8_PAD;
 constexpr int RU8_BYTES = RU8_U + 2 * QCAP_U8 * 2;
 constexpr int RI32_J = HDR_BYTES, RI32_I = RI32_J + BI32_PAD, RI32_U = RI32_I + BI32_PAD;
-constexpr int RI32_BYTES = RI32_U + BI32_PAD;
+constexpr int RI32_BYTES = RI32_U + 2 * QCAP_R * 2;
 constexpr int E_W = HDR_BYTES, E_U = E_W + BI32_PAD;
 constexpr int E_BYTES = E_U + 2 * QCAP_E * 2;
 static_assert(RU8_JW % 128 == 0 && RU8_IW % 128 == 0 && RI32_J % 128 == 0 && RI32_I % 128 == 0 && RI32_U % 128 == 0 &&
                   E_U % 128 == 0 && E_W % 128 == 0,
               "TMA destinations must be 128-byte aligned");
-static_assert(2 * QCAP_R * 2 <= BI32_PAD &&
+static_assert(
                   BU8_PAD <= 2 * QCAP_E * 2,
               "queues must fit the staging union");
 
@@ -94,7 +94,7 @@ constexpr int FAM_SMEM[FAM_COUNT] = {RU8_BYTES, RI32_BYTES, E_BYTES,
 constexpr int FAM_NT[FAM_COUNT] = {64, 64, 128, 128};
 // resident CTAs per SM that each family's shared memory allows; the
 // register budget is sized for them
-constexpr int FAM_MINB[FAM_COUNT] = {14, 3, 8, 3};
+constexpr int FAM_MINB[FAM_COUNT] = {14, 5, 8, 5};
 
 // neighbourhood offsets (dy, dx); 8-connected: the first 4 are N+ (raster)
 __device__ __forceinline__ int nb_dy(int conn, int k) {
@@ -805,7 +805,6 @@ __device__ bool recon_i32_visit(const KArgs &ka, const JobDesc *jd, int gt, char
     uint64_t *bar = (uint64_t *)(sm + 256);
     int *JB = (int *)(sm + RI32_J);
     int *IB = (int *)(sm + RI32_I);
-    int *OB = (int *)(sm + RI32_U);  // second J source, later the queues
     uint16_t *Q0 = (uint16_t *)(sm + RI32_U), *Q1 = Q0 + QCAP_R;
     const int tid = threadIdx.x;
     const int lt = gt - jd->tile_base, tx = lt % jd->tiles_x, ty = lt / jd->tiles_x;
@@ -819,43 +818,48 @@ __device__ bool recon_i32_visit(const KArgs &ka, const JobDesc *jd, int gt, char
     begin_visit(hdr);
     make_offsets<CONN, BI32_W>(hdr);
     __syncthreads();
-    int need_m = 0, need_o = 0;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        need_m |= hdr[H_SRC + k] == 0;
-        need_o |= hdr[H_SRC + k] == 1;
-    }
     const bool first = hdr[H_SRC + 4] == 0;
-    int *odst = need_m ? OB : JB;  // marker -> JB; current result -> OB, or JB alone
+    const int *jsrc = first ? mk : out;
+    const int64_t jpitch = first ? jd->pa : jd->po;
+
+    // 1. stage the mask box and the box of the tile's own J source (marker
+    //    on a first visit, the current result later); the boxes are the
+    //    working layout
     if (jd->use_tma) {
         if (tid == 0) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, BI32_BYTES * (1 + need_m + need_o));
+            mbar_arrive_expect_tx(bar, 2 * BI32_BYTES);
             tma_load_2d(IB, &jd->tm[1], x0 - 4, y0 - 1, bar);
-            if (need_m) tma_load_2d(JB, &jd->tm[0], x0 - 4, y0 - 1, bar);
-            if (need_o) tma_load_2d(odst, &jd->tm[2], x0 - 4, y0 - 1, bar);
+            tma_load_2d(JB, &jd->tm[first ? 0 : 2], x0 - 4, y0 - 1, bar);
         }
         if (!wait_boxes(bar, phase, deadline, ka.ctl)) return false;
     } else {
         stage_plain<int, BI32_W>(IB, ms, jd->pb, jd->h, jd->w, x0 - 4, y0 - 1, NT);
-        if (need_m) stage_plain<int, BI32_W>(JB, mk, jd->pa, jd->h, jd->w, x0 - 4, y0 - 1, NT);
-        if (need_o) stage_plain<int, BI32_W>(odst, out, jd->po, jd->h, jd->w, x0 - 4, y0 - 1, NT);
+        stage_plain<int, BI32_W>(JB, jsrc, jpitch, jd->h, jd->w, x0 - 4, y0 - 1, NT);
         __syncthreads();
     }
-    // merge the sources, clip by the mask, and give cells outside the image
-    // the lowest value (they then never raise or get raised)
-    for (int i = tid; i < RR * BI32_W; i += NT) {
-        const int r = i / BI32_W, c = i - r * BI32_W - 3;
-        const int gy = y0 - 1 + r, gx = x0 - 1 + c;
-        if (c < 0 || c >= RR || gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w) {
-            JB[i] = INT_MIN;
-            IB[i] = INT_MIN;
-            continue;
+    // cells outside the image take the lowest value in J and I, so they
+    // never raise or get raised; only tiles at the image edge have them
+    if (x0 == 0 || y0 == 0 || x0 + TS >= jd->w || y0 + TS >= jd->h) {
+        for (int i = tid; i < RR * BI32_W; i += NT) {
+            const int r = i / BI32_W, c = i - r * BI32_W - 3;
+            const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+            if (gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w) {
+                JB[i] = INT_MIN;
+                IB[i] = INT_MIN;
+            }
         }
-        const int reg = region(r) * 3 + region(c);
-        const int v = (need_m && need_o && hdr[H_SRC + reg] == 1) ? OB[i] : JB[i];
-        JB[i] = min(v, IB[i]);
+        __syncthreads();
     }
+    // halo cells from the other buffer, halo clipped by the mask; the
+    // interior is clipped here on a first visit without sweeps (otherwise
+    // the first row pass clips every interior pixel)
+    halo_fixup<int, NT>(jd, JB, IB, hdr, first, x0, y0, I32Grid::cell);
+    if (first && ka.sweeps == 0)
+        for (int k = tid; k < TS * TS; k += NT) {
+            const int i = I32Grid::cell(k / TS + 1, k % TS + 1);
+            if (JB[i] > IB[i]) JB[i] = IB[i];
+        }
     __syncthreads();
 
     pc.mark(hdr, 0);
