@@ -462,7 +462,7 @@ int iwpp_ctx_create(iwpp_ctx **out, int device, size_t hbm_budget_bytes) {
     ctx->opt.max_relaunch = 1;
     ctx->opt.timeout_ms = 10000;
     ctx->opt.revisit_sweep_min = 0;
-    ctx->opt.edt_sweeps = 1;
+    ctx->opt.edt_sweeps = 2;
     ctx->opt.edt_revisit_sweep_min = 64;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
@@ -761,7 +761,7 @@ int iwpp_plan_autotune(iwpp_plan *p, void *stream, int reps, iwpp_options *best)
     // sweep candidates per operation; a mixed plan pairs them up
     const int sweeps_c[3] = {2, 3, 4};
     const int revisit_c[2] = {0, 32};
-    const int edt_sweeps_c[3] = {0, 1, 2};
+    const int edt_sweeps_c[3] = {1, 2, 3};
     const int edt_revisit_c[2] = {16, 64};
     const int fam = p->P.fam;
     const int bps_c[2] = {0, occ > 2 ? occ - 1 : 0};

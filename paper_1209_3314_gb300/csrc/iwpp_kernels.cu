@@ -950,24 +950,18 @@ struct Pick {
     }
 };
 
-// Row passes of the distance-transform sweep (one thread per row): each
-// pixel keeps the better of its own feature and its left (then right)
-// neighbour's, as Danielsson's raster vector propagation does.
-__device__ __forceinline__ bool edt_row_passes(unsigned *__restrict__ V, int r, int oy, int ox) {
+// Row pass of the distance-transform sweep (one thread per row, DIR +1
+// left to right, -1 right to left): each pixel keeps the better of its own
+// feature and the previous pixel's, as Danielsson's raster vector
+// propagation does.
+template <int DIR>
+__device__ __forceinline__ bool edt_row_pass(unsigned *__restrict__ V, int r, int oy, int ox) {
     const int base = r * EP + 3, y = oy + r;
     bool ch = false;
-    unsigned run = V[base];
+    unsigned run = V[base + (DIR > 0 ? 0 : TS + 1)];
 #pragma unroll 4
-    for (int c = 1; c <= TS; ++c) {
-        const unsigned f = V[base + c];
-        Pick p(f, y, ox + c);
-        p.consider(run, y, ox + c);
-        if (p.best != f) { V[base + c] = p.best; ch = true; }
-        run = p.best;
-    }
-    run = V[base + TS + 1];
-#pragma unroll 4
-    for (int c = TS; c >= 1; --c) {
+    for (int s = 1; s <= TS; ++s) {
+        const int c = DIR > 0 ? s : TS + 1 - s;
         const unsigned f = V[base + c];
         Pick p(f, y, ox + c);
         p.consider(run, y, ox + c);
@@ -985,8 +979,8 @@ __device__ __forceinline__ bool edt_row_passes(unsigned *__restrict__ V, int r, 
 // candidate, and keeping them off the running feature's dependency chain
 // leaves only the vertical candidate's test on it.
 template <int DIR>
-__device__ __forceinline__ bool edt_column_pass(unsigned *__restrict__ V, int oy, int ox) {
-    const int c = threadIdx.x + 1, x = ox + c;
+__device__ __forceinline__ bool edt_column_pass(unsigned *__restrict__ V, int oy, int ox, int t) {
+    const int c = t + 1, x = ox + c;
     const int r0 = DIR > 0 ? 0 : RR - 1;
     unsigned up = V[ecell(r0, c)];
     bool ch = false;
@@ -1005,16 +999,36 @@ __device__ __forceinline__ bool edt_column_pass(unsigned *__restrict__ V, int oy
     return ch;
 }
 
-// One sweep set (rows both ways, columns down and up); block-uniform
-// "changed" result.  A set that changes nothing proves the tile stable.
+// One sweep set on 128 threads: threads 0..63 run the left-to-right row
+// pass and then the downward column pass, threads 64..127 the right-to-left
+// row pass and then the upward column pass, at the same time.  A pixel
+// written by both halves keeps one of the two candidates (a valid feature
+// either way; later steps use compare-and-swap and so only improve it).
+// Block-uniform "changed" result: a set that changes nothing wrote nothing,
+// so every pixel was compared with all 8 neighbours' current features and
+// the tile is stable.
+template <int NT>
 __device__ bool edt_sweep_set(unsigned *V, int oy, int ox) {
     const int t = threadIdx.x;
     bool ch = false;
-    if (t < TS) ch |= edt_row_passes(V, t + 1, oy, ox);
-    __syncthreads();
-    if (t < TS) {
-        ch |= edt_column_pass<+1>(V, oy, ox);
-        ch |= edt_column_pass<-1>(V, oy, ox);
+    if (NT >= 2 * TS) {
+        if (t < TS) {
+            ch |= edt_row_pass<+1>(V, t + 1, oy, ox);
+            ch |= edt_column_pass<+1>(V, oy, ox, t);
+        } else if (t < 2 * TS) {
+            ch |= edt_row_pass<-1>(V, t - TS + 1, oy, ox);
+            ch |= edt_column_pass<-1>(V, oy, ox, t - TS);
+        }
+    } else {
+        if (t < TS) {
+            ch |= edt_row_pass<+1>(V, t + 1, oy, ox);
+            ch |= edt_row_pass<-1>(V, t + 1, oy, ox);
+        }
+        __syncthreads();
+        if (t < TS) {
+            ch |= edt_column_pass<+1>(V, oy, ox, t);
+            ch |= edt_column_pass<-1>(V, oy, ox, t);
+        }
     }
     return __syncthreads_or(ch) != 0;
 }
@@ -1163,7 +1177,7 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, QCAP_E, ka.spill_cap};
     auto sweeps_then_dilate = [&]() -> unsigned {
         bool changed = true;
-        for (int s = 0; s < ka.edt_sweeps && changed; ++s) changed = edt_sweep_set(V, oy, ox);
+        for (int s = 0; s < ka.edt_sweeps && changed; ++s) changed = edt_sweep_set<NT>(V, oy, ox);
         if (!changed && ka.edt_sweeps > 0) return 0u;
         return edt_dilate_seed<NT>(V, oy, ox, q0, off);
     };

@@ -102,7 +102,7 @@ def test_autotune_keeps_results(cuda_ctx):
     plan = cuda_ctx.plan(jobs)
     try:
         best = plan.autotune(reps=2)
-        assert 2 <= best["sweeps"] <= 4 and 0 <= best["edt_sweeps"] <= 2
+        assert 2 <= best["sweeps"] <= 4 and 1 <= best["edt_sweeps"] <= 3
         for j in jobs:
             if j["op"] == "recon":
                 j["out"].fill_(0)
