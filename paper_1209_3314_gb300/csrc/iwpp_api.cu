@@ -366,6 +366,14 @@ JobDesc edt_job(const iwpp_image *bin, int32_t *sq, int32_t *nn, int flags) {
     d.pa = bin->pitch;
     d.sqdist = sq;
     d.nearest = nn;
+    // division by the width through a multiply and a shift: with
+    // l = ceil(log2 w) and m = floor(2^(32+l) / w) + 1, (n * m) >> (32 + l)
+    // equals n / w for every n < 2^32 (m*w - 2^(32+l) lies in (0, w], so the
+    // added fraction stays below 1/w); n < 2^31 keeps n * m below 2^64
+    int l = 0;
+    while ((1ll << l) < (long long)d.w) ++l;
+    d.wdiv_m = (1ull << (32 + l)) / (unsigned long long)d.w + 1ull;
+    d.wdiv_s = 32 + l;
     return d;
 }
 

@@ -33,6 +33,10 @@ struct alignas(64) JobDesc {
     int32_t *sqdist;     // edt outputs (dense, pitch w)
     int32_t *nearest;
     int64_t pa, pb, po;  // pitches in elements
+    // n / w for 0 <= n < 2^31 as (n * wdiv_m) >> wdiv_s (distance transform:
+    // linear feature index -> row)
+    unsigned long long wdiv_m;
+    int wdiv_s;
 };
 
 struct alignas(64) KArgs {

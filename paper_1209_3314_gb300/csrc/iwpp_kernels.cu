@@ -911,6 +911,12 @@ __device__ __forceinline__ bool better(unsigned dn, unsigned f, int qy, int qx, 
 __device__ __forceinline__ bool is_feature(uint8_t b, int flags) { return (flags & 1) ? b != 0 : b == 0; }
 
 constexpr int EP = BI32_W;  // VR row stride (words)
+
+// row of a linear feature index (0 <= idx < 2^31) through the job's
+// multiply-and-shift divisor
+__device__ __forceinline__ int div_w(const JobDesc *jd, int idx) {
+    return (int)(((unsigned long long)(unsigned)idx * jd->wdiv_m) >> jd->wdiv_s);
+}
 __device__ __forceinline__ int ecell(int r, int c) { return r * EP + c + 3; }
 
 // Can the feature of cell (pr, pc) improve its interior neighbour n?  With
@@ -1154,7 +1160,7 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
             if (hdr[H_SRC + region(r) * 3 + region(c)] == 1) {
                 const int idx = (int)V[i];
                 if (idx >= 0) {
-                    const int fy = idx / jd->w;
+                    const int fy = div_w(jd, idx);
                     v = pack_yx(fy, idx - fy * jd->w);
                 }
             } else if (is_feature(BB[r * BU8_W + c + 15], jd->flags)) {
@@ -1272,7 +1278,7 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
             unsigned cq;
             if (hdr[H_SRC + reg] == 1) {
                 const int idx = raw[u];
-                const int fy = idx / jd->w;
+                const int fy = div_w(jd, idx);
                 cq = idx < 0 ? (unsigned)VR_INF : pack_yx(fy, idx - fy * jd->w);
             } else {
                 cq = is_feature((uint8_t)raw[u], jd->flags) ? pack_yx(gy, gx) : (unsigned)VR_INF;
