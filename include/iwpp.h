@@ -101,7 +101,9 @@ typedef struct {
                                 sets per bulk visit (0 = queue only)          */
     int32_t edt_revisit_sweep_min; /* distance transform: a later visit sweeps
                                 when more halo pixels than this changed       */
-    int32_t reserved[5];
+    int32_t revisit_sweeps;  /* reconstruction: sweep sets on a later visit
+                                (-1: the same as sweeps)                      */
+    int32_t reserved[4];
 } iwpp_options;
 
 /* Creates a context on `device`.  hbm_budget_bytes bounds the workspace the

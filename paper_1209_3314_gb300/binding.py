@@ -49,7 +49,8 @@ class Options(ctypes.Structure):
                 ("spill_cap", ctypes.c_int32), ("max_relaunch", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("revisit_sweep_min", ctypes.c_int32), ("edt_sweeps", ctypes.c_int32),
-                ("edt_revisit_sweep_min", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("edt_revisit_sweep_min", ctypes.c_int32), ("revisit_sweeps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Request(ctypes.Structure):

@@ -238,6 +238,7 @@ int prepare(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, const iwpp_options &opt, 
     ka.revisit_sweep_min = opt.revisit_sweep_min;
     ka.edt_sweeps = opt.edt_sweeps;
     ka.edt_revisit_sweep_min = opt.edt_revisit_sweep_min;
+    ka.revisit_sweeps = opt.revisit_sweeps < 0 ? opt.sweeps : opt.revisit_sweeps;
     ka.timeout_ns = (unsigned long long)opt.timeout_ms * 1000000ull;
     return IWPP_OK;
 }
@@ -472,6 +473,7 @@ int iwpp_ctx_create(iwpp_ctx **out, int device, size_t hbm_budget_bytes) {
     ctx->opt.revisit_sweep_min = 0;
     ctx->opt.edt_sweeps = 2;
     ctx->opt.edt_revisit_sweep_min = 64;
+    ctx->opt.revisit_sweeps = -1;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&ctx->ctl, sizeof(Control)) != cudaSuccess ||
@@ -513,7 +515,8 @@ int iwpp_set_options(iwpp_ctx *ctx, const iwpp_options *o) {
     if (o->blocks_per_sm < 0 || o->sweeps < 0 || o->sweeps > 64 || o->queue_factor < 1 || o->queue_factor > 4096 ||
         o->spill_cap < 0 || o->spill_cap > (1 << 20) || o->max_relaunch < 0 || o->max_relaunch > 64 ||
         o->timeout_ms < 1 || o->timeout_ms > 600000 || o->timing < 0 || o->timing > 1 ||
-        o->revisit_sweep_min < 0 || o->edt_sweeps < 0 || o->edt_sweeps > 64 || o->edt_revisit_sweep_min < 0)
+        o->revisit_sweep_min < 0 || o->edt_sweeps < 0 || o->edt_sweeps > 64 || o->edt_revisit_sweep_min < 0 ||
+        o->revisit_sweeps < -1 || o->revisit_sweeps > 64)
         return fail(ctx, IWPP_EINVAL, "option out of range");
     ctx->opt = *o;
     return IWPP_OK;

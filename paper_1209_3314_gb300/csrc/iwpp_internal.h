@@ -52,6 +52,7 @@ struct alignas(64) KArgs {
     int revisit_sweep_min;  // later visits sweep when more halo seeds than this
     int edt_sweeps;       // the same two settings for the distance transform
     int edt_revisit_sweep_min;
+    int revisit_sweeps;   // reconstruction: sweep sets on a later visit
     unsigned long long timeout_ns;
 };
 

@@ -590,16 +590,16 @@ __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t 
                                 const int *off, PhaseClock &pc, unsigned long long deadline) {
     uint16_t *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
     RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, G::QCAP, ka.spill_cap};
-    auto sweeps_then_dilate = [&](const RQ &q) -> unsigned {
+    auto sweeps_then_dilate = [&](const RQ &q, int sets) -> unsigned {
         bool changed = true;
-        for (int s = 0; s < ka.sweeps && changed; ++s) changed = g.sweep(CONN);
+        for (int s = 0; s < sets && changed; ++s) changed = g.sweep(CONN);
         // a sweep set that changed nothing proves the tile stable
-        if (!changed && ka.sweeps > 0) return 0u;
+        if (!changed && sets > 0) return 0u;
         return g.template dilate<CONN, NT>(q, off);
     };
     unsigned seeds;
     if (first) {
-        seeds = sweeps_then_dilate(q0);
+        seeds = sweeps_then_dilate(q0, ka.sweeps);
     } else {
         // later visit: only the halo changed.  A few entry points are
         // cheapest as queue seeds; many mean a bulk change, which the
@@ -610,7 +610,7 @@ __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t 
             __syncthreads();
             if (threadIdx.x == 0) { hdr[H_CNT0] = 0; hdr[H_RESCAN] = 0; }
             __syncthreads();
-            seeds = sweeps_then_dilate(q0);
+            seeds = sweeps_then_dilate(q0, ka.revisit_sweeps);
         }
     }
     if ((threadIdx.x & 31) == 0) atomicAdd(hdr + H_SEEDS, (int)seeds);

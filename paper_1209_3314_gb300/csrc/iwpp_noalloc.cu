@@ -142,7 +142,8 @@ extern "C" int iwpp_recon_u8_noalloc(const uint8_t *marker, int64_t marker_pitch
     ka.ctl = (Control *)(base + kCtl);
     ka.spill = (uint16_t *)(base + kSpill);
     ka.spill_cap = kSpillCap;
-    ka.sweeps = 2;
+    ka.sweeps = 3;
+    ka.revisit_sweeps = 3;
     ka.revisit_sweep_min = 0;
     ka.timeout_ns = 10000000000ull;
     int grid = slot->occupancy * slot->sm_count;

@@ -110,6 +110,23 @@ def test_tma_and_plain_staging_agree(cuda_ctx):
         edt_parity(img, sq, nn)
 
 
+def test_largest_side_and_beyond(cuda_ctx):
+    """Sides of 32768 (the largest the packed feature coordinates allow) as
+    a row, a column and a 3-row strip against the exact EDT; one pixel more
+    and empty images are rejected."""
+    for shape in ((1, 32768), (32768, 1), (3, 32768)):
+        rng = np.random.default_rng(sum(shape))
+        b = (rng.random(shape) < 0.999).astype(np.uint8)
+        b.flat[-1] = 0  # a feature in the last pixel at least
+        sq, nn = run(cuda_ctx, b)
+        edt_parity(b, sq, nn, exact=oracle.edt_exact(b, False))
+        assert nn.flat[-1] == b.size - 1 and sq.flat[-1] == 0
+    for shape in ((1, 32769), (32769, 1), (0, 4), (4, 0)):
+        with pytest.raises(IWPPError) as e:
+            cuda_ctx.edt(torch.zeros(shape, dtype=torch.uint8, device=DEV))
+        assert e.value.code == -1
+
+
 def test_invalid_arguments_raise(cuda_ctx):
     b = torch.zeros((8, 8), dtype=torch.uint8, device=DEV)
     s = torch.zeros((8, 8), dtype=torch.int32, device=DEV)

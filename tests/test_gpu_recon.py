@@ -78,10 +78,13 @@ def test_config_4096_and_int32_variant(cuda_ctx):
     np.testing.assert_array_equal(run(cuda_ctx, J, I, 8), ref.astype(np.int32) * 1000 - 70000)
 
 
-@pytest.mark.parametrize("sweeps", [0, 1, 3])
-def test_sweep_count_does_not_change_result(cuda_ctx, sweeps):
+@pytest.mark.parametrize("sweeps,revisit_sweeps,revisit_min",
+                         [(0, -1, 0), (1, -1, 0), (3, -1, 0), (3, 0, 0), (3, 1, 0), (2, 2, 1 << 20)])
+def test_sweep_count_does_not_change_result(cuda_ctx, sweeps, revisit_sweeps, revisit_min):
     marker, mask = synth.recon_inputs(700, 513, 6.0, 50, seed=21)
-    np.testing.assert_array_equal(run(cuda_ctx, marker, mask, 8, sweeps=sweeps), oracle.fh(marker, mask, 8))
+    got = run(cuda_ctx, marker, mask, 8, sweeps=sweeps, revisit_sweeps=revisit_sweeps,
+              revisit_sweep_min=revisit_min)
+    np.testing.assert_array_equal(got, oracle.fh(marker, mask, 8))
 
 
 def test_in_place_and_pitched(cuda_ctx):
@@ -176,6 +179,24 @@ def test_degenerate_shapes_and_values(cuda_ctx):
     c = np.full((150, 170), 200, np.uint8)
     j = rng.integers(0, 150, c.shape).astype(np.uint8)
     np.testing.assert_array_equal(run(cuda_ctx, j, c, 8), np.full(c.shape, j.max(), np.uint8))
+
+
+def test_extreme_aspect_ratios(cuda_ctx):
+    """One row or one column of thousands of tiles (ragged last tile)."""
+    rng = np.random.default_rng(3)
+    for h, w in ((1, 200_003), (200_003, 1), (3, 70_001)):
+        I = rng.integers(0, 256, (h, w)).astype(np.uint8)
+        J = np.maximum(I.astype(np.int16) - rng.integers(0, 60, (h, w)), 0).astype(np.uint8)
+        for conn in (4, 8):
+            np.testing.assert_array_equal(run(cuda_ctx, J, I, conn), oracle.fh(J, I, conn))
+
+
+def test_empty_images_are_rejected(cuda_ctx):
+    for shape in ((0, 5), (5, 0), (0, 0)):
+        a = torch.zeros(shape, dtype=torch.uint8, device=DEV)
+        with pytest.raises(IWPPError) as e:
+            cuda_ctx.recon(a, a.clone(), out=torch.zeros(shape, dtype=torch.uint8, device=DEV))
+        assert e.value.code == -1
 
 
 def test_invalid_arguments_raise(cuda_ctx):
