@@ -358,6 +358,59 @@ def bench_served(ctx, dev, rates, duration, budget):
             "sizes": "square sides log-uniform 512..8192, alternating recon / EDT", "rates": results}
 
 
+def bench_queue_ablation(ctx, dev, reps=5):
+    """Intra-tile queue designs on the paper's Table 1 kind of workload: a
+    4-connected reconstruction of a 4096^2 image (blurred noise, sigma 8,
+    marker = mask - 60), the queue carrying the propagation.  The number of
+    sweep sets before seeding varies the initial queue, as the paper varies
+    its initial raster scans.  Every mode gives the same (exact) result."""
+    import statistics
+
+    import numpy as np
+    import torch
+
+    from paper_1209_3314_gb300 import synth
+
+    marker, mask = synth.recon_inputs(4096, 4096, 8.0, 60, seed=1000)
+    d_marker = torch.from_numpy(marker).to(dev)
+    d_mask = torch.from_numpy(mask).to(dev)
+    out = torch.empty_like(d_mask)
+    old = ctx.options()
+    modes = {0: "warp-aggregated -> shared block queue -> global spill",
+             1: "per-thread shared atomics -> shared block queue -> global spill",
+             2: "warp-aggregated -> global queue only",
+             3: "per-thread atomics -> global queue only"}
+    ref = None
+    rows = []
+    st = torch.cuda.current_stream(dev)
+    try:
+        for sweeps in (0, 1, 3):
+            for mode in modes:
+                ctx.set_options(sweeps=sweeps, revisit_sweeps=-1, queue_mode=mode, timing=0)
+                ctx.recon(d_marker, d_mask, 4, out=out)
+                if ref is None:
+                    ref = out.clone()
+                same = bool(torch.equal(out, ref))
+                ctx.stats_reset()
+                times = []
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(st)
+                    ctx.recon(d_marker, d_mask, 4, out=out, sync=False)
+                    b.record(st)
+                    ctx.sync()
+                    times.append(a.elapsed_time(b))
+                q = ctx.stats()
+                rows.append({"sweeps": sweeps, "mode": mode, "ms": round(statistics.median(times), 3),
+                             "seeds": q["seeds"] // reps, "pushes": q["pushes"] // reps,
+                             "spills": q["spills"] // reps, "rounds": q["rounds"] // reps,
+                             "tiles": q["tiles_processed"] // reps, "same_result": same})
+    finally:
+        ctx.set_options(**old)
+    return {"workload": "4096x4096 uint8 reconstruction, 4-connected, sigma 8, marker = mask - 60",
+            "modes": modes, "runs": rows}
+
+
 def run_gpu(args, ws, rank, local):
     import numpy as np
     import torch
@@ -508,6 +561,9 @@ def run_gpu(args, ws, rank, local):
     batched = served = None
     if rank == 0 and not args.skip_batched:
         batched = bench_batched(ctx, dev, args.batch_images, max(1, args.steps // 2))
+    ablation = None
+    if rank == 0 and not args.skip_ablation:
+        ablation = bench_queue_ablation(ctx, dev)
     if rank == 0 and not args.skip_served:
         rates = [int(r) for r in args.serve_rates.split(",") if r]
         served = bench_served(ctx, dev, rates, args.serve_duration, 120 << 30)
@@ -536,6 +592,7 @@ def run_gpu(args, ws, rank, local):
                                          "spills", "rescans", "relaunches", "rounds")},
             "batched": batched,
             "served": served,
+            "queue_ablation": ablation,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_val, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3), "check": ok},
@@ -559,6 +616,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-served", action="store_true")
+    ap.add_argument("--skip-ablation", action="store_true")
     ap.add_argument("--batch-images", type=int, default=512)
     ap.add_argument("--serve-rates", default="200,500,1000,2000")
     ap.add_argument("--serve-duration", type=float, default=1.0)

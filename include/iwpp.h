@@ -103,7 +103,17 @@ typedef struct {
                                 when more halo pixels than this changed       */
     int32_t revisit_sweeps;  /* reconstruction: sweep sets on a later visit
                                 (-1: the same as sweeps)                      */
-    int32_t reserved[4];
+    int32_t queue_mode;      /* intra-tile queue design, for ablations (the
+                                result is the same in every mode):
+                                0  warp-aggregated pushes (ballot / prefix
+                                   sum, one shared atomic per warp) into the
+                                   block queue in shared memory, spilling to
+                                   the CTA's queue in global memory
+                                1  one shared atomic per pushing thread
+                                2  warp-aggregated, block queue bypassed:
+                                   every item in the global queue
+                                3  both                                       */
+    int32_t reserved[3];
 } iwpp_options;
 
 /* Creates a context on `device`.  hbm_budget_bytes bounds the workspace the

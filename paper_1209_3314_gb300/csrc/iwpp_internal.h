@@ -53,6 +53,7 @@ struct alignas(64) KArgs {
     int edt_sweeps;       // the same two settings for the distance transform
     int edt_revisit_sweep_min;
     int revisit_sweeps;   // reconstruction: sweep sets on a later visit
+    int queue_mode;       // queue ablation: bit 0 per-thread atomics, bit 1 global-only
     unsigned long long timeout_ns;
 };
 

@@ -206,6 +206,7 @@ struct RQ {
     int *count;
     int *rescan;
     int cap_s, cap_g;
+    int per_thread;  // queue ablation: one shared atomic per pushing thread
 };
 
 __device__ __forceinline__ void rq_put(const RQ &q, int pos, int item) {
@@ -221,11 +222,23 @@ __device__ __forceinline__ int rq_get(const uint16_t *s, const uint16_t *g, int 
 // Warp-aggregated enqueue: each lane holds up to 9 items as a neighbour bit
 // mask (its per-thread queue; bit 8 is the pixel itself); an inclusive warp
 // scan of the counts gives each lane its slots and the last lane reserves
-// the warp's total with one shared atomic.  Called by all 32 lanes.
+// the warp's total with one shared atomic.  Called by all 32 lanes.  With
+// q.per_thread (queue ablation) every pushing lane reserves its own slots.
 __device__ __forceinline__ unsigned warp_enqueue(unsigned mask, int p, const int *off, const RQ &q) {
     const int lane = threadIdx.x & 31;
     const int cnt = __popc(mask);
     if (!__any_sync(0xffffffffu, cnt)) return 0;
+    if (q.per_thread) {
+        if (cnt) {
+            int pos = atomicAdd(q.count, cnt);
+            while (mask) {
+                const int k = __ffs(mask) - 1;
+                mask &= mask - 1;
+                rq_put(q, pos++, p + off[k]);
+            }
+        }
+        return __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+    }
     int incl = cnt;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -250,7 +263,8 @@ __device__ __forceinline__ unsigned warp_enqueue(unsigned mask, int p, const int
 // rescan(q): re-seeds the whole tile into q, returns the count.
 template <int NT, int NB, typename Proc, typename Rescan>
 __device__ void run_rounds(int *hdr, uint16_t *Q0, uint16_t *Q1, int qcap, uint16_t *spill, int spill_cap,
-                           const int *off, Proc proc, Rescan rescan, unsigned long long deadline, Control *ctl) {
+                           const int *off, Proc proc, Rescan rescan, unsigned long long deadline, Control *ctl,
+                           int per_thread) {
     const int tid = threadIdx.x;
     int cur = 0;
     unsigned pushed = 0, spilled = 0, rescans = 0, rounds = 0;
@@ -280,7 +294,7 @@ __device__ void run_rounds(int *hdr, uint16_t *Q0, uint16_t *Q1, int qcap, uint1
         const uint16_t *qs = cur ? Q1 : Q0;
         const uint16_t *qg = spill + cur * spill_cap;
         RQ out{cur ? Q0 : Q1, spill + (cur ^ 1) * spill_cap, hdr + H_CNT0 + (cur ^ 1), hdr + H_RESCAN, qcap,
-               spill_cap};
+               spill_cap, per_thread};
         // neighbour-parallel: lane task k handles neighbour k % NB of item
         // k / NB, so small frontiers still fill the lanes and each lane's
         // critical path is one neighbour test
@@ -589,7 +603,9 @@ template <int CONN, int NT, typename G>
 __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t *Q0, uint16_t *Q1, bool first,
                                 const int *off, PhaseClock &pc, unsigned long long deadline) {
     uint16_t *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
-    RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, G::QCAP, ka.spill_cap};
+    // block-queue capacity: 0 in the global-only queue ablation
+    const int qcap = (ka.queue_mode & 2) ? 0 : G::QCAP;
+    RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, qcap, ka.spill_cap, ka.queue_mode & 1};
     auto sweeps_then_dilate = [&](const RQ &q, int sets) -> unsigned {
         bool changed = true;
         for (int s = 0; s < sets && changed; ++s) changed = g.sweep(CONN);
@@ -624,7 +640,8 @@ __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t 
         return g.j(qi) < v && g.raise(qi, v);
     };
     auto rescan = [&](const RQ &q) -> unsigned { return g.template dilate<CONN, NT>(q, off); };
-    run_rounds<NT, CONN>(hdr, Q0, Q1, G::QCAP, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl);
+    run_rounds<NT, CONN>(hdr, Q0, Q1, qcap, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl,
+                         ka.queue_mode & 1);
     pc.mark(hdr, 2);
 }
 
@@ -1180,7 +1197,8 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     //    halo changed; a few entry points seed the queue directly, many
     //    mean a bulk change handled as on a first visit.
     uint16_t *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
-    RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, QCAP_E, ka.spill_cap};
+    const int qcap = (ka.queue_mode & 2) ? 0 : QCAP_E;
+    RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, qcap, ka.spill_cap, ka.queue_mode & 1};
     auto sweeps_then_dilate = [&]() -> unsigned {
         bool changed = true;
         for (int s = 0; s < ka.edt_sweeps && changed; ++s) changed = edt_sweep_set<NT>(V, oy, ox);
@@ -1211,7 +1229,8 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
         return edt_try(V, oy, ox, pr, pc2, f, n, true);
     };
     auto rescan = [&](const RQ &q) -> unsigned { return edt_seed_scan<NT>(V, oy, ox, q, true, off); };
-    run_rounds<NT, 8>(hdr, Q0, Q1, QCAP_E, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl);
+    run_rounds<NT, 8>(hdr, Q0, Q1, qcap, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl,
+                      ka.queue_mode & 1);
     __syncthreads();
     pc.mark(hdr, 2);
 

@@ -75,6 +75,14 @@ def test_sweep_settings_keep_parity(cuda_ctx, edt_sweeps, revisit):
         edt_parity(wl.binary, sq, nn, fnz)
 
 
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_queue_modes_keep_parity(cuda_ctx, mode):
+    wl = synth.config_workload("edt4096", size=600)
+    for fnz in (False, True):
+        sq, nn = run(cuda_ctx, wl.binary, fnz, queue_mode=mode, edt_sweeps=0)
+        edt_parity(wl.binary, sq, nn, fnz)
+
+
 def test_figure3_fixture(cuda_ctx):
     with open(os.path.join(GOLDEN, "edt_departure_170.json")) as f:
         g = json.load(f)

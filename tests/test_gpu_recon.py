@@ -87,6 +87,21 @@ def test_sweep_count_does_not_change_result(cuda_ctx, sweeps, revisit_sweeps, re
     np.testing.assert_array_equal(got, oracle.fh(marker, mask, 8))
 
 
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_queue_modes_give_the_same_result(cuda_ctx, mode):
+    """The queue-ablation modes (per-thread atomics, global-only queue)
+    change how items are queued, never the result; no sweeps, so the queue
+    carries the whole propagation."""
+    marker, mask = synth.recon_inputs(700, 513, 6.0, 50, seed=22)
+    for conn in (4, 8):
+        got = run(cuda_ctx, marker, mask, conn, queue_mode=mode, sweeps=0)
+        np.testing.assert_array_equal(got, oracle.fh(marker, mask, conn))
+    J = marker.astype(np.int32) * 7 - 900
+    I = mask.astype(np.int32) * 7 - 900
+    np.testing.assert_array_equal(run(cuda_ctx, J, I, 8, queue_mode=mode, sweeps=1),
+                                  oracle.fh(marker, mask, 8).astype(np.int32) * 7 - 900)
+
+
 def test_in_place_and_pitched(cuda_ctx):
     marker, mask = synth.recon_inputs(333, 301, 4.0, 40, seed=8)
     ref = oracle.fh(marker, mask, 8)
