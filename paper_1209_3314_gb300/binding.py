@@ -84,6 +84,7 @@ SIGNATURES = {
                                 ctypes.POINTER(Image), _vp]),
     "iwpp_edt": (_i32, [_vp, ctypes.POINTER(Image), _vp, _vp, _i32, _vp]),
     "iwpp_edt_async": (_i32, [_vp, ctypes.POINTER(Image), _vp, _vp, _i32, _vp]),
+    "iwpp_edt_exact": (_i32, [_vp, ctypes.POINTER(Image), _vp, _vp, _i32, _vp]),
     "iwpp_recon_batched": (_i32, [_vp, _i32, ctypes.POINTER(Image), ctypes.POINTER(Image), _i32,
                                   ctypes.POINTER(Image), _vp]),
     "iwpp_edt_batched": (_i32, [_vp, _i32, ctypes.POINTER(Image), ctypes.POINTER(_vp),
@@ -254,9 +255,11 @@ class Context:
         return out
 
     def edt(self, binary, feature_nonzero: bool = False, sqdist=None, nearest=None,
-            stream=None, sync: bool = True):
+            stream=None, sync: bool = True, exact: bool = False):
         """Distance transform of a uint8 CUDA tensor.  Returns
-        (sqdist int32, nearest int32 linear index)."""
+        (sqdist int32, nearest int32 linear index).  exact=True runs the
+        exact separable transform (iwpp_edt_exact, synchronous) instead of
+        the propagation method."""
         torch = _torch()
         h, w = binary.shape
         if sqdist is None:
@@ -267,7 +270,7 @@ class Context:
             if t.dtype != torch.int32 or tuple(t.shape) != (h, w) or not t.is_contiguous() or not t.is_cuda:
                 raise ValueError("sqdist/nearest must be contiguous int32 CUDA tensors of the image shape")
         b = image_of(binary)
-        fn = self.lib.iwpp_edt if sync else self.lib.iwpp_edt_async
+        fn = self.lib.iwpp_edt_exact if exact else (self.lib.iwpp_edt if sync else self.lib.iwpp_edt_async)
         flags = IWPP_EDT_FEATURE_NONZERO if feature_nonzero else IWPP_EDT_FEATURE_ZERO
         self._check(fn(self.h, ctypes.byref(b), ctypes.c_void_p(sqdist.data_ptr()),
                        ctypes.c_void_p(nearest.data_ptr()), flags, _stream_ptr(stream)))

@@ -558,6 +558,40 @@ int iwpp_edt(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist, int32_t *
     return run(ctx, jobs, (cudaStream_t)stream, true);
 }
 
+int iwpp_edt_exact(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist, int32_t *nearest, int flags,
+                   void *stream) {
+    if (!ctx) return IWPP_EINVAL;
+    int rc = check_edt(ctx, binary, sqdist, nearest, flags);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int h = binary->h, w = binary->w, nb = exact_bands(h);
+    const size_t band_bytes = align_up((size_t)nb * w * sizeof(int32_t), 256);
+    const size_t stack_bytes = (size_t)h * w * sizeof(uint32_t);
+    if ((rc = ensure_ws(ctx, 4 * band_bytes + stack_bytes, st))) return rc;
+    char *ws = (char *)ctx->ws;
+    ExactArgs a;
+    a.bin = (const uint8_t *)binary->data;
+    a.pitch = binary->pitch;
+    a.h = h;
+    a.w = w;
+    a.flags = flags;
+    a.nb = nb;
+    a.first = (int32_t *)ws;
+    a.last = (int32_t *)(ws + band_bytes);
+    a.above = (int32_t *)(ws + 2 * band_bytes);
+    a.below = (int32_t *)(ws + 3 * band_bytes);
+    a.stack = (uint32_t *)(ws + 4 * band_bytes);
+    a.G = nearest;
+    a.sqdist = sqdist;
+    a.nearest = nearest;
+    CK(launch_edt_exact(a, st), "exact distance transform launch");
+    ctx->launches += 4;
+    ctx->calls += 1;
+    CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return IWPP_OK;
+}
+
 int iwpp_recon_batched(iwpp_ctx *ctx, int n, const iwpp_image *markers, const iwpp_image *masks, int conn,
                        iwpp_image *outs, void *stream) {
     if (!ctx) return IWPP_EINVAL;

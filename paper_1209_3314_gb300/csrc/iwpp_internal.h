@@ -57,6 +57,19 @@ struct alignas(64) KArgs {
     unsigned long long timeout_ns;
 };
 
+// Exact separable distance transform (iwpp_edt_exact.cu).
+struct ExactArgs {
+    const uint8_t *bin;
+    int64_t pitch;        // binary image pitch in bytes
+    int h, w, flags, nb;  // nb: bands of the column pass
+    int32_t *first, *last, *above, *below;  // nb x w band summaries
+    int32_t *G;           // h x w: row of the nearest feature in the column (the nearest output)
+    uint32_t *stack;      // h x w scratch: the row pass's envelope stacks
+    int32_t *sqdist, *nearest;
+};
+int exact_bands(int h);
+cudaError_t launch_edt_exact(const ExactArgs &a, cudaStream_t s);
+
 // Launch helpers implemented in iwpp_kernels.cu.
 int family_threads(int fam);
 int family_smem(int fam);
