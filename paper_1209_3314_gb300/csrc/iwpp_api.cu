@@ -567,8 +567,9 @@ int iwpp_edt_exact(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist, int
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     const int h = binary->h, w = binary->w, nb = exact_bands(h);
     const size_t band_bytes = align_up((size_t)nb * w * sizeof(int32_t), 256);
-    const size_t stack_bytes = (size_t)h * w * sizeof(uint32_t);
-    if ((rc = ensure_ws(ctx, 4 * band_bytes + stack_bytes, st))) return rc;
+    const size_t plane_bytes = align_up((size_t)h * w * sizeof(uint32_t), 256);
+    const size_t flag_bytes = align_up((size_t)h * sizeof(int), 256);
+    if ((rc = ensure_ws(ctx, 4 * band_bytes + 2 * plane_bytes + flag_bytes, st))) return rc;
     char *ws = (char *)ctx->ws;
     ExactArgs a;
     a.bin = (const uint8_t *)binary->data;
@@ -581,12 +582,13 @@ int iwpp_edt_exact(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist, int
     a.last = (int32_t *)(ws + band_bytes);
     a.above = (int32_t *)(ws + 2 * band_bytes);
     a.below = (int32_t *)(ws + 3 * band_bytes);
-    a.stack = (uint32_t *)(ws + 4 * band_bytes);
-    a.G = nearest;
+    a.G = (int32_t *)(ws + 4 * band_bytes);
+    a.stack = (uint32_t *)(ws + 4 * band_bytes + plane_bytes);
+    a.rowflag = (int *)(ws + 4 * band_bytes + 2 * plane_bytes);
     a.sqdist = sqdist;
     a.nearest = nearest;
     CK(launch_edt_exact(a, st), "exact distance transform launch");
-    ctx->launches += 4;
+    ctx->launches += 6;
     ctx->calls += 1;
     CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     return IWPP_OK;

@@ -23,6 +23,11 @@ namespace {
 
 constexpr int XT = 128;  // columns per CTA in the column kernels
 constexpr int BH = 256;  // rows per band in the column pass
+constexpr int SW = 256;   // pixels per row segment in the windowed row passes (threads per CTA)
+constexpr int WB = 256;   // search radius of the first windowed row pass
+constexpr int SR = 8;     // rows per CTA in the first windowed row pass
+constexpr int WB2 = 4096; // search radius of the second windowed row pass
+constexpr int UNSETTLED = -2;  // sqdist marker of a pixel left to the next pass
 
 __device__ __forceinline__ bool feature_px(uint8_t b, int flags) {
     return (flags & 1) ? b != 0 : b == 0;
@@ -99,13 +104,111 @@ __device__ __forceinline__ void cross(uint32_t ea, uint32_t eb, long long &num, 
     den = 2 * (vb - va);
 }
 
+// Outward search from pixel x of row y over the staged column-pass
+// results g (g[i] is column base + i; -1: no site), one column offset d at
+// a time up to radius rad, keeping the nearest site.  Once d^2 is no
+// smaller than the best squared distance found, no site farther out can be
+// nearer, so the pixel is settled exactly; it is also settled when the
+// window covers the whole row.  Returns settled; best / bc / bg describe
+// the nearest site found (bc < 0: none).
+__device__ __forceinline__ bool window_search(const int *g, int base, int x, int y, int w, int rad, long long &best,
+                                              int &bc, int &bg) {
+    best = LLONG_MAX;
+    bc = bg = -1;
+    int d = 0;
+    for (; d <= rad; ++d) {
+        const long long dd = (long long)d * d;
+        if (dd >= best) break;
+        const int gl = g[x - base - d];
+        if (gl >= 0) {
+            const long long c = dd + (long long)(y - gl) * (y - gl);
+            if (c < best) { best = c; bc = x - d; bg = gl; }
+        }
+        if (d > 0) {
+            const int gr = g[x - base + d];
+            if (gr >= 0) {
+                const long long c = dd + (long long)(y - gr) * (y - gr);
+                if (c < best) { best = c; bc = x + d; bg = gr; }
+            }
+        }
+    }
+    // d is the offset the loop stopped at (rad + 1 when it ran out)
+    return (long long)d * d >= best || (x - rad <= 0 && x + rad >= w - 1);
+}
+
+// Stages columns base .. base + n - 1 of G's row y (-1 outside the image).
+__device__ __forceinline__ void stage_row(int *g, const int32_t *Grow, int base, int n, int w) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int c = base + i;
+        g[i] = (c >= 0 && c < w) ? Grow[c] : -1;
+    }
+}
+
+__device__ __forceinline__ void write_site(const ExactArgs &a, int y, int x, long long best, int bc, int bg) {
+    const int64_t o = (int64_t)y * a.w + x;
+    a.sqdist[o] = bc < 0 ? INT_MAX : (int)best;
+    a.nearest[o] = bc < 0 ? -1 : bg * a.w + bc;
+}
+
+// First windowed row pass: a CTA takes SW pixels of SR rows, stages the
+// column-pass results of those columns and WB columns on either side, and
+// searches with radius WB.  A pixel left unsettled is marked in sqdist and
+// flags its row (rowflag 1) for the second pass.
+__global__ void rows_window_kernel(ExactArgs a) {
+    __shared__ int g[SW + 2 * WB];
+    const int x0 = blockIdx.x * SW, x = x0 + threadIdx.x;
+    const int base = x0 - WB;  // column of g[0]
+    for (int rr = 0; rr < SR; ++rr) {
+        const int y = blockIdx.y * SR + rr;
+        if (y >= a.h) break;
+        __syncthreads();
+        stage_row(g, a.G + (int64_t)y * a.w, base, SW + 2 * WB, a.w);
+        __syncthreads();
+        if (x >= a.w) continue;
+        long long best;
+        int bc, bg;
+        if (window_search(g, base, x, y, a.w, WB, best, bc, bg)) {
+            write_site(a, y, x, best, bc, bg);
+        } else {
+            a.sqdist[(int64_t)y * a.w + x] = UNSETTLED;
+            a.rowflag[y] = 1;
+        }
+    }
+}
+
+// Second windowed row pass, on flagged rows only: radius WB2 for the
+// marked pixels; a pixel still unsettled flags its row (rowflag 2) for the
+// exact envelope pass.
+__global__ void rows_window2_kernel(ExactArgs a) {
+    extern __shared__ int g2[];
+    const int x0 = blockIdx.x * SW, x = x0 + threadIdx.x;
+    const int base = x0 - WB2;
+    for (int rr = 0; rr < SR; ++rr) {
+        const int y = blockIdx.y * SR + rr;
+        if (y >= a.h) break;
+        if (a.rowflag[y] == 0) continue;  // block-uniform
+        const int64_t o = (int64_t)y * a.w + x;
+        const bool mine = x < a.w && a.sqdist[o] == UNSETTLED;
+        if (!__syncthreads_or(mine)) continue;
+        stage_row(g2, a.G + (int64_t)y * a.w, base, SW + 2 * WB2, a.w);
+        __syncthreads();
+        if (mine) {
+            long long best;
+            int bc, bg;
+            if (window_search(g2, base, x, y, a.w, WB2, best, bc, bg)) write_site(a, y, x, best, bc, bg);
+            else a.rowflag[y] = 2;
+        }
+        __syncthreads();  // g2 is restaged for the next row
+    }
+}
+
 // One thread per row: the lower envelope of the row's sites (Felzenszwalb
 // and Huttenlocher's sweep, with exact rational comparisons), then the
-// nearest site of every pixel.  The row's G values are all read before its
-// outputs are written, so G may be the nearest-index output itself.
+// nearest site of every pixel.  Runs on the rows the windowed passes left
+// unsettled (rowflag 2).
 __global__ void rows_kernel(ExactArgs a) {
     const int y = blockIdx.x * blockDim.x + threadIdx.x;
-    if (y >= a.h) return;
+    if (y >= a.h || a.rowflag[y] != 2) return;
     const int w = a.w;
     const int32_t *Grow = a.G + (int64_t)y * w;
     uint32_t *S = a.stack + (int64_t)y * w;
@@ -155,9 +258,16 @@ int exact_bands(int h) { return (h + BH - 1) / BH; }
 cudaError_t launch_edt_exact(const ExactArgs &a, cudaStream_t s) {
     cudaGetLastError();
     const dim3 gx((a.w + XT - 1) / XT), gxb((a.w + XT - 1) / XT, a.nb);
+    cudaError_t e = cudaMemsetAsync(a.rowflag, 0, (size_t)a.h * sizeof(int), s);
+    if (e != cudaSuccess) return e;
     band_ends_kernel<<<gxb, XT, 0, s>>>(a);
     band_links_kernel<<<gx, XT, 0, s>>>(a);
     columns_kernel<<<gxb, XT, 0, s>>>(a);
+    rows_window_kernel<<<dim3((a.w + SW - 1) / SW, (a.h + SR - 1) / SR), SW, 0, s>>>(a);
+    const int smem2 = (SW + 2 * WB2) * (int)sizeof(int);
+    e = cudaFuncSetAttribute(rows_window2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
+    if (e != cudaSuccess) return e;
+    rows_window2_kernel<<<dim3((a.w + SW - 1) / SW, (a.h + SR - 1) / SR), SW, smem2, s>>>(a);
     rows_kernel<<<(a.h + 31) / 32, 32, 0, s>>>(a);
     return cudaGetLastError();
 }
