@@ -411,6 +411,36 @@ def bench_queue_ablation(ctx, dev, reps=5):
             "modes": modes, "runs": rows}
 
 
+def bench_edt_exact(ctx, dev, d_bin, npx, reps=3):
+    """The exact separable EDT (iwpp_edt_exact) on the same binary image,
+    both feature polarities, beside the propagation EDT of the same
+    polarity: per-call CUDA-event times (median)."""
+    import statistics
+
+    import torch
+
+    st = torch.cuda.current_stream(dev)
+    sq = torch.empty(d_bin.shape, dtype=torch.int32, device=dev)
+    nn = torch.empty_like(sq)
+    res = {}
+    for fnz in (False, True):
+        row = {}
+        for exact in (True, False):
+            ctx.edt(d_bin, fnz, sqdist=sq, nearest=nn, exact=exact)
+            times = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                ctx.edt(d_bin, fnz, sqdist=sq, nearest=nn, exact=exact, sync=exact)
+                b.record(st)
+                ctx.sync()
+                times.append(a.elapsed_time(b))
+            ms = statistics.median(times)
+            row["exact" if exact else "propagation"] = {"ms": round(ms, 3), "mpx_s": round(npx / ms / 1e3, 1)}
+        res["features_nonzero" if fnz else "features_zero"] = row
+    return res
+
+
 def run_gpu(args, ws, rank, local):
     import numpy as np
     import torch
@@ -561,6 +591,9 @@ def run_gpu(args, ws, rank, local):
     batched = served = None
     if rank == 0 and not args.skip_batched:
         batched = bench_batched(ctx, dev, args.batch_images, max(1, args.steps // 2))
+    exact = None
+    if rank == 0 and not args.skip_exact:
+        exact = bench_edt_exact(ctx, dev, d_bin, npx)
     ablation = None
     if rank == 0 and not args.skip_ablation:
         ablation = bench_queue_ablation(ctx, dev)
@@ -593,6 +626,7 @@ def run_gpu(args, ws, rank, local):
             "batched": batched,
             "served": served,
             "queue_ablation": ablation,
+            "edt_exact": exact,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_val, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3), "check": ok},
@@ -617,6 +651,7 @@ def main():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-served", action="store_true")
     ap.add_argument("--skip-ablation", action="store_true")
+    ap.add_argument("--skip-exact", action="store_true")
     ap.add_argument("--batch-images", type=int, default=512)
     ap.add_argument("--serve-rates", default="200,500,1000,2000")
     ap.add_argument("--serve-duration", type=float, default=1.0)
