@@ -441,6 +441,44 @@ def bench_edt_exact(ctx, dev, d_bin, npx, reps=3):
     return res
 
 
+def bench_coverage(ctx, dev, d_marker, d_mask, side, reps=3):
+    """The 16384^2 reconstruction with tissue covering 25, 50, 75 and 100 %
+    of the image (smooth blob-shaped regions; background 0 in marker and
+    mask), as the paper's Section 5.2.3 varies tissue coverage."""
+    import statistics
+
+    import torch
+
+    from paper_1209_3314_gb300 import synth
+
+    st = torch.cuda.current_stream(dev)
+    out = torch.empty_like(d_mask)
+    rows_out = []
+    for cov in (0.25, 0.5, 0.75, 1.0):
+        keep, rows, cols = synth.tissue_cells(side, side, cov, seed=2100)
+        region = torch.from_numpy(keep).to(dev)[torch.from_numpy(rows).to(dev)][:, torch.from_numpy(cols).to(dev)]
+        region = region.to(torch.uint8)
+        mk, ms = d_marker * region, d_mask * region
+        ctx.recon(mk, ms, 8, out=out)
+        ctx.stats_reset()
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            ctx.recon(mk, ms, 8, out=out, sync=False)
+            b.record(st)
+            ctx.sync()
+            times.append(a.elapsed_time(b))
+        q = ctx.stats()
+        ms_ = statistics.median(times)
+        rows_out.append({"coverage": cov, "tissue_px": int(region.sum().item()), "ms": round(ms_, 3),
+                         "mpx_s": round(side * side / ms_ / 1e3, 1),
+                         "tiles_per_call": q["tiles_processed"] // reps})
+        del region, mk, ms
+    return {"workload": f"{side}x{side} reconstruction (8-conn) masked to tissue regions; same mask and marker",
+            "runs": rows_out}
+
+
 def run_gpu(args, ws, rank, local):
     import numpy as np
     import torch
@@ -591,6 +629,9 @@ def run_gpu(args, ws, rank, local):
     batched = served = None
     if rank == 0 and not args.skip_batched:
         batched = bench_batched(ctx, dev, args.batch_images, max(1, args.steps // 2))
+    coverage = None
+    if rank == 0 and not args.skip_coverage:
+        coverage = bench_coverage(ctx, dev, d_marker, d_mask, side)
     exact = None
     if rank == 0 and not args.skip_exact:
         exact = bench_edt_exact(ctx, dev, d_bin, npx)
@@ -627,6 +668,7 @@ def run_gpu(args, ws, rank, local):
             "served": served,
             "queue_ablation": ablation,
             "edt_exact": exact,
+            "coverage": coverage,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_val, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3), "check": ok},
@@ -652,6 +694,7 @@ def main():
     ap.add_argument("--skip-served", action="store_true")
     ap.add_argument("--skip-ablation", action="store_true")
     ap.add_argument("--skip-exact", action="store_true")
+    ap.add_argument("--skip-coverage", action="store_true")
     ap.add_argument("--batch-images", type=int, default=512)
     ap.add_argument("--serve-rates", default="200,500,1000,2000")
     ap.add_argument("--serve-duration", type=float, default=1.0)

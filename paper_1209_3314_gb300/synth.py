@@ -32,6 +32,9 @@ __all__ = [
     "config_workload",
     "batched_workloads",
     "served_pool",
+    "tissue_cells",
+    "tissue_region",
+    "apply_tissue",
 ]
 
 
@@ -246,3 +249,40 @@ def served_pool(side: int = 8192, seed: int = 4000):
     marker, mask = recon_inputs(side, side, 8.0, 50, seed)
     img, _ = disks_binary(side, side, 4, 40, 0.25, seed + 1)
     return marker, mask, img
+
+
+def tissue_cells(h: int, w: int, coverage: float, seed: int, cells: int = 256):
+    """The low-resolution form of tissue_region: (keep, rows, cols) with
+    keep a cells x cells boolean map, rows[y] / cols[x] the cell row /
+    column of image row y / column x; the region is keep[rows][:, cols].
+
+    A cells x cells field of U[0,1) noise is blurred (Gaussian, sigma = 4
+    cells); pixel (y, x) belongs to cell (y*cells//h, x*cells//w).  Cells
+    are taken in order of decreasing value (ties by index) until the pixels
+    they cover reach coverage * h * w (coverage 1: everything)."""
+    rows = (np.arange(h) * cells) // h
+    cols = (np.arange(w) * cells) // w
+    if coverage >= 1.0:
+        return np.ones((cells, cells), dtype=bool), rows, cols
+    rng = np.random.default_rng(seed)
+    f = _blur_axis(_blur_axis(rng.random((cells, cells), dtype=np.float64), 4.0, 1), 4.0, 0)
+    weight = np.outer(np.bincount(rows, minlength=cells), np.bincount(cols, minlength=cells)).ravel()
+    order = np.argsort(-f.ravel(), kind="stable")
+    k = int(np.searchsorted(np.cumsum(weight[order]), coverage * h * w))
+    keep = np.zeros(cells * cells, dtype=bool)
+    keep[order[:k + 1]] = True
+    return keep.reshape(cells, cells), rows, cols
+
+
+def tissue_region(h: int, w: int, coverage: float, seed: int, cells: int = 256) -> np.ndarray:
+    """Boolean tissue map covering `coverage` of an h x w image in smooth,
+    blob-shaped regions (the paper's images are partly background); see
+    tissue_cells for the construction."""
+    keep, rows, cols = tissue_cells(h, w, coverage, seed, cells)
+    return keep[rows][:, cols]
+
+
+def apply_tissue(marker: np.ndarray, mask: np.ndarray, region: np.ndarray):
+    """(marker, mask) with everything outside the tissue region set to 0."""
+    return marker * region.astype(marker.dtype), mask * region.astype(mask.dtype)
+

@@ -206,6 +206,16 @@ def test_extreme_aspect_ratios(cuda_ctx):
             np.testing.assert_array_equal(run(cuda_ctx, J, I, conn), oracle.fh(J, I, conn))
 
 
+@pytest.mark.parametrize("cov", [0.25, 0.6])
+def test_partial_tissue_coverage(cuda_ctx, cov):
+    """Tissue-masked images (background 0 in marker and mask), the kind the
+    coverage benchmark times."""
+    marker, mask = synth.recon_inputs(1500, 1300, 8.0, 50, seed=31)
+    marker, mask = synth.apply_tissue(marker, mask, synth.tissue_region(1500, 1300, cov, seed=32))
+    for conn in (4, 8):
+        np.testing.assert_array_equal(run(cuda_ctx, marker, mask, conn), oracle.fh(marker, mask, conn))
+
+
 def test_empty_images_are_rejected(cuda_ctx):
     for shape in ((0, 5), (5, 0), (0, 0)):
         a = torch.zeros(shape, dtype=torch.uint8, device=DEV)

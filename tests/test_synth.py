@@ -41,3 +41,29 @@ def test_batched_workloads_shapes():
     assert [w.op for w in wls] == ["recon", "edt"] * 3
     for w in wls:
         assert 32 <= w.h <= 64 and 32 <= w.w <= 64
+
+
+def test_tissue_region_coverage_and_shape():
+    for h, w in ((1000, 777), (64, 5000)):
+        for cov in (0.25, 0.5, 0.75):
+            r = synth.tissue_region(h, w, cov, seed=11)
+            assert r.shape == (h, w) and r.dtype == bool
+            # cells are taken whole: the overshoot is below one cell's pixels
+            cell_px = -(-h // 256) * -(-w // 256)
+            assert cov * h * w <= r.sum() <= cov * h * w + cell_px
+        assert synth.tissue_region(h, w, 1.0, seed=11).all()
+    a = synth.tissue_region(512, 512, 0.5, seed=3)
+    b = synth.tissue_region(512, 512, 0.5, seed=3)
+    assert np.array_equal(a, b)
+    # blob-shaped: most region pixels have their right neighbour in the region
+    assert (a[:, 1:] & a[:, :-1]).sum() > 0.9 * a[:, 1:].sum()
+
+
+def test_apply_tissue_zeroes_the_background():
+    marker, mask = synth.recon_inputs(300, 200, 4.0, 40, seed=5)
+    r = synth.tissue_region(300, 200, 0.5, seed=6)
+    m2, k2 = synth.apply_tissue(marker, mask, r)
+    assert m2.dtype == np.uint8 and k2.dtype == np.uint8
+    assert (m2[~r] == 0).all() and (k2[~r] == 0).all()
+    assert np.array_equal(m2[r], marker[r]) and np.array_equal(k2[r], mask[r])
+
