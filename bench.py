@@ -550,6 +550,29 @@ def run_gpu(args, ws, rank, local):
     dom_ms = e_med if dominant == "edt" else r_med
     launches = st["kernel_launches"]
 
+    # the int32 variant of the reconstruction workload (same values
+    # widened), per-call CUDA-event times
+    recon_i32 = None
+    if rank == 0:
+        i_marker = d_marker.to(torch.int32)
+        i_mask = d_mask.to(torch.int32)
+        i_out = torch.empty_like(i_mask)
+        ctx.recon(i_marker, i_mask, 8, out=i_out)
+        ti = []
+        for _ in range(3):
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            ctx.recon(i_marker, i_mask, 8, out=i_out, sync=False)
+            b_.record(stream)
+            ctx.sync()
+            ti.append(a_.elapsed_time(b_))
+        ms_i = statistics.median(ti)
+        recon_i32 = {"ms": round(ms_i, 4), "mpx_s": round(npx / ms_i / 1e3, 1),
+                     "gbs": round(12 * npx / (ms_i * 1e-3) / 1e9, 1),
+                     "frac_hbm": round(12 * npx / (ms_i * 1e-3) / 1e9 / peak, 4),
+                     "exact_vs_uint8": bool(torch.equal(i_out.to(torch.uint8), d_out))}
+        del i_marker, i_mask, i_out
+
     # ---- end to end through the public API with host buffers.  Two slots
     # (context, stream, device buffers, pinned result buffers) take steps
     # in turn, so one step's host<->device copies overlap the other's
@@ -664,6 +687,11 @@ def run_gpu(args, ws, rank, local):
                          "kernel_ms_mean_per_call": round(kern_ms, 4)},
             "queue": {k: st[k] for k in ("tiles_processed", "tiles_initial", "seeds", "pushes",
                                          "spills", "rescans", "relaunches", "rounds")},
+            # time inside tile visits, summed over CTAs (CTA-ms per call):
+            # staging, sweeps + seeding, queue rounds, store + border test
+            "phase_cta_ms_per_call": {n: round(v / 1e6 / calls, 1) for n, v in
+                                      zip(("staging", "sweeps_seeds", "rounds", "store_border"), st["phase_ns"])},
+            "recon_int32": recon_i32,
             "batched": batched,
             "served": served,
             "queue_ablation": ablation,
