@@ -394,24 +394,41 @@ __device__ __forceinline__ bool u8_row_passes(uint8_t *__restrict__ J, const uin
     return a || b;
 }
 
-// Row passes for int32 rows (one thread per row).
-__device__ __forceinline__ bool i32_row_passes(int *__restrict__ J, const int *__restrict__ I, int base) {
+// Row passes for int32 rows (one thread per row).  The 64 interior cells
+// (16-byte aligned: a row is 288 bytes and cell 1 sits at word 4) come as
+// 16-byte chunks of four cells, worked on in registers and stored back
+// only if changed; the chunk loop stays rolled.
+template <int DIR>
+__device__ __forceinline__ bool i32_row_pass(int *__restrict__ J, const int *__restrict__ I, int base) {
+    int4 *jp = (int4 *)(J + base + 1);  // cells 1 .. 64
+    const int4 *ip = (const int4 *)(I + base + 1);
+    int run = J[base + (DIR > 0 ? 0 : TS + 1)];
     bool ch = false;
-    int run = J[base];
-    for (int c = 1; c <= TS; ++c) {
-        const int o = J[base + c];
-        const int v = min(I[base + c], max(o, run));
-        if (v != o) { J[base + c] = v; ch = true; }
-        run = v;
-    }
-    run = J[base + TS + 1];
-    for (int c = TS; c >= 1; --c) {
-        const int o = J[base + c];
-        const int v = min(I[base + c], max(o, run));
-        if (v != o) { J[base + c] = v; ch = true; }
-        run = v;
+#pragma unroll 1
+    for (int s = 0; s < TS / 4; ++s) {
+        const int k = DIR > 0 ? s : TS / 4 - 1 - s;
+        const int4 a = jp[k], m = ip[k];
+        int v[4] = {a.x, a.y, a.z, a.w};
+        const int mm[4] = {m.x, m.y, m.z, m.w};
+        bool d = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = DIR > 0 ? q : 3 - q;
+            const int nv = min(mm[c], max(v[c], run));
+            d |= nv != v[c];
+            v[c] = nv;
+            run = nv;
+        }
+        if (d) jp[k] = make_int4(v[0], v[1], v[2], v[3]);
+        ch |= d;
     }
     return ch;
+}
+
+__device__ __forceinline__ bool i32_row_passes(int *__restrict__ J, const int *__restrict__ I, int base) {
+    const bool a = i32_row_pass<+1>(J, I, base);
+    const bool b = i32_row_pass<-1>(J, I, base);
+    return a || b;
 }
 
 // Column pass (N^{0,+} downwards when DIR = +1, N^{0,-} upwards when -1) for
@@ -884,11 +901,24 @@ __device__ bool recon_i32_visit(const KArgs &ka, const JobDesc *jd, int gt, char
     const int *off = hdr + H_OFF;
     recon_propagate<CONN, NT>(ka, g, hdr, Q0, Q1, first, off, pc, deadline);
     __syncthreads();
+    // store the interior rows, four pixels per 16-byte store where the
+    // TMA maps guarantee 16-byte aligned rows
     load_sources(ka, jd, tx, ty, hdr);
-    for (int i = tid; i < TS * TS; i += NT) {
-        const int r = i / TS, c = i - r * TS;
-        const int gy = y0 + r, gx = x0 + c;
-        if (gy < jd->h && gx < jd->w) out[(int64_t)gy * jd->po + gx] = JB[I32Grid::cell(r + 1, c + 1)];
+    {
+        const bool vec = jd->use_tma != 0;
+        for (int i = tid; i < TS * TS / 4; i += NT) {
+            const int r = i >> 4, q = i & 15;
+            const int gy = y0 + r, gx = x0 + 4 * q;
+            if (gy >= jd->h || gx >= jd->w) continue;
+            const int4 v = *(const int4 *)(JB + I32Grid::cell(r + 1, 4 * q + 1));
+            int *dst = out + (int64_t)gy * jd->po + gx;
+            if (vec && gx + 4 <= jd->w) {
+                *(int4 *)dst = v;
+            } else {
+                const int vv[4] = {v.x, v.y, v.z, v.w};
+                for (int b = 0; b < 4 && gx + b < jd->w; ++b) dst[b] = vv[b];
+            }
+        }
     }
     __syncthreads();
     publish_tile(ka, gt, hdr);
