@@ -137,10 +137,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# the translation unit of the persistent tile kernels (the kernels whose
+# DRAM traffic profiles/traffic.json records)
+KERNEL_SOURCES = ("iwpp_kernels.cu", "iwpp_internal.h", "iwpp_device.cuh", "iwpp_tma.cuh")
+
+
 def source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1209_3314_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in KERNEL_SOURCES:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())

@@ -161,81 +161,4 @@ __device__ inline void tq_finish(const TileQueue &q, Control *ctl, int t) {
     }
 }
 
-// ---------------------------------------------------- intra-tile queues
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-// The out-queue of one propagation round, seen as one virtual array whose
-// first `cap_s` entries live in shared memory (BQ) and the next `cap_g` in
-// the CTA's global spill buffer (GBQ).  Entries beyond both are dropped and
-// `*rescan` is set.
-struct RoundQueue {
-    int *smem;        // BQ (shared)
-    int *gmem;        // GBQ (global, per CTA)
-    int *count;       // shared counter of reserved entries
-    int *rescan;      // shared flag
-    int cap_s, cap_g;
-};
-
-__device__ __forceinline__ void rq_store(const RoundQueue &rq, int pos, int item) {
-    if (pos < rq.cap_s) rq.smem[pos] = item;
-    else if (pos - rq.cap_s < rq.cap_g) rq.gmem[pos - rq.cap_s] = item;
-    else *rq.rescan = 1;
-}
-
-__device__ __forceinline__ int rq_load(const int *smem, const int *gmem, int cap_s, int i) {
-    return i < cap_s ? smem[i] : __ldcg(gmem + (i - cap_s));
-}
-
-// Per-warp staging queue (32..63 entries in shared memory).  push() must be
-// called by all 32 lanes together; `n` is the warp-uniform fill level kept
-// in a register.  A full batch of 32 goes to the round queue with a single
-// shared atomic (warp-aggregated enqueue).
-struct WarpQueue {
-    int *buf;         // 64 entries of this warp
-    int n;            // fill level (warp-uniform)
-    unsigned pushed;  // insertions made through this queue (warp-uniform)
-
-    __device__ __forceinline__ void flush32(const RoundQueue &rq) {
-        const int lane = threadIdx.x & 31;
-        int base = 0;
-        if (lane == 0) base = atomicAdd(rq.count, 32);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        __syncwarp();
-        rq_store(rq, base + lane, buf[lane]);
-        int moved = (lane + 32 < n) ? buf[lane + 32] : 0;
-        __syncwarp();
-        if (lane + 32 < n) buf[lane] = moved;
-        __syncwarp();
-        n -= 32;
-    }
-
-    __device__ __forceinline__ void push(bool pred, int item, const RoundQueue &rq) {
-        unsigned m = __ballot_sync(0xffffffffu, pred);
-        if (m == 0) return;
-        if (pred) buf[n + __popc(m & lanemask_lt())] = item;
-        n += __popc(m);
-        pushed += __popc(m);
-        __syncwarp();
-        if (n >= 32) flush32(rq);
-    }
-
-    // Remaining entries (< 32) at the end of a round.
-    __device__ __forceinline__ void drain(const RoundQueue &rq) {
-        const int lane = threadIdx.x & 31;
-        if (n == 0) return;
-        int base = 0;
-        if (lane == 0) base = atomicAdd(rq.count, n);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        __syncwarp();
-        if (lane < n) rq_store(rq, base + lane, buf[lane]);
-        __syncwarp();
-        n = 0;
-    }
-};
-
 }  // namespace iwpp
