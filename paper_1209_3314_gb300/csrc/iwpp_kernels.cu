@@ -1016,6 +1016,10 @@ __device__ __forceinline__ bool edt_row_pass(unsigned *__restrict__ V, int r, in
     for (int s = 1; s <= TS; ++s) {
         const int c = DIR > 0 ? s : TS + 1 - s;
         const unsigned f = V[base + c];
+        if (f == pack_yx(y, ox + c)) {  // a feature is its own nearest
+            run = f;
+            continue;
+        }
         Pick p(f, y, ox + c);
         p.consider(run, y, ox + c);
         if (p.best != f) { V[base + c] = p.best; ch = true; }
@@ -1042,6 +1046,10 @@ __device__ __forceinline__ bool edt_column_pass(unsigned *__restrict__ V, int oy
         const int r = DIR > 0 ? s : RR - 1 - s;
         const int i = ecell(r, c), y = oy + r, ip = i - DIR * EP;
         const unsigned f = V[i];
+        if (f == pack_yx(y, x)) {  // a feature is its own nearest
+            up = f;
+            continue;
+        }
         Pick p(f, y, x);
         p.consider(V[ip - 1], y, x);
         p.consider(V[ip + 1], y, x);
