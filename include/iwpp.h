@@ -113,7 +113,12 @@ typedef struct {
                                 2  warp-aggregated, block queue bypassed:
                                    every item in the global queue
                                 3  both                                       */
-    int32_t reserved[3];
+    int32_t test_empty_slot; /* tests of the timeout path only: 1 leaves one
+                                slot of the initial tile queue unfilled, so
+                                one claim waits until timeout_ms runs out and
+                                the call returns IWPP_ETIMEOUT (no fault, no
+                                hang: every device wait is bounded)           */
+    int32_t reserved[2];
 } iwpp_options;
 
 /* Creates a context on `device`.  hbm_budget_bytes bounds the workspace the

@@ -50,7 +50,8 @@ class Options(ctypes.Structure):
                 ("timeout_ms", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("revisit_sweep_min", ctypes.c_int32), ("edt_sweeps", ctypes.c_int32),
                 ("edt_revisit_sweep_min", ctypes.c_int32), ("revisit_sweeps", ctypes.c_int32),
-                ("queue_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("queue_mode", ctypes.c_int32), ("test_empty_slot", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Request(ctypes.Structure):

@@ -240,6 +240,7 @@ int prepare(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, const iwpp_options &opt, 
     ka.edt_revisit_sweep_min = opt.edt_revisit_sweep_min;
     ka.revisit_sweeps = opt.revisit_sweeps < 0 ? opt.sweeps : opt.revisit_sweeps;
     ka.queue_mode = opt.queue_mode;
+    ka.test_empty_slot = opt.test_empty_slot;
     ka.timeout_ns = (unsigned long long)opt.timeout_ms * 1000000ull;
     return IWPP_OK;
 }
@@ -517,7 +518,8 @@ int iwpp_set_options(iwpp_ctx *ctx, const iwpp_options *o) {
         o->spill_cap < 0 || o->spill_cap > (1 << 20) || o->max_relaunch < 0 || o->max_relaunch > 64 ||
         o->timeout_ms < 1 || o->timeout_ms > 600000 || o->timing < 0 || o->timing > 1 ||
         o->revisit_sweep_min < 0 || o->edt_sweeps < 0 || o->edt_sweeps > 64 || o->edt_revisit_sweep_min < 0 ||
-        o->revisit_sweeps < -1 || o->revisit_sweeps > 64 || o->queue_mode < 0 || o->queue_mode > 3)
+        o->revisit_sweeps < -1 || o->revisit_sweeps > 64 || o->queue_mode < 0 || o->queue_mode > 3 ||
+        o->test_empty_slot < 0 || o->test_empty_slot > 1)
         return fail(ctx, IWPP_EINVAL, "option out of range");
     ctx->opt = *o;
     return IWPP_OK;

@@ -54,6 +54,7 @@ struct alignas(64) KArgs {
     int edt_revisit_sweep_min;
     int revisit_sweeps;   // reconstruction: sweep sets on a later visit
     int queue_mode;       // queue ablation: bit 0 per-thread atomics, bit 1 global-only
+    int test_empty_slot;  // timeout-path tests: initial queue slot 0 left unfilled
     unsigned long long timeout_ns;
 };
 

@@ -1450,7 +1450,10 @@ __global__ void fill_queue_kernel(const __grid_constant__ KArgs ka, int first) {
     const int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)ka.tq.cap; i += stride) {
         if (i < ka.ntiles) {
-            ka.tq.slots[initial_slot(job_of(ka, i), i)] = i;
+            const int slot = initial_slot(job_of(ka, i), i);
+            // timeout-path tests: slot 0 stays empty, so its claim waits out
+            // the deadline and the launch ends with ST_TIMEOUT
+            ka.tq.slots[slot] = (ka.test_empty_slot && slot == 0) ? -1 : i;
             ka.tq.state[i] = TS_QUEUED;
             if (first) ka.tq.visited[i] = 0;
         } else {

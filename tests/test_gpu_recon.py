@@ -216,6 +216,30 @@ def test_partial_tissue_coverage(cuda_ctx, cov):
         np.testing.assert_array_equal(run(cuda_ctx, marker, mask, conn), oracle.fh(marker, mask, conn))
 
 
+def test_device_wait_timeout_is_reported_and_the_context_stays_usable(cuda_ctx):
+    """Failure detection without a fault: one initial tile-queue slot is left
+    empty, so one claim waits until the (short) deadline runs out; every CTA
+    ends within its own deadline, the call returns ETIMEOUT, and the next
+    call on the same context is correct."""
+    import time
+
+    marker, mask = synth.recon_inputs(600, 700, 6.0, 50, seed=42)
+    old = cuda_ctx.options()
+    cuda_ctx.set_options(timeout_ms=200, test_empty_slot=1)
+    try:
+        t0 = time.perf_counter()
+        with pytest.raises(IWPPError) as e:
+            run(cuda_ctx, marker, mask, 8)
+        assert e.value.code == -4
+        assert time.perf_counter() - t0 < 30.0
+    finally:
+        cuda_ctx.set_options(**old)
+    np.testing.assert_array_equal(run(cuda_ctx, marker, mask, 8), oracle.fh(marker, mask, 8))
+    b = (synth.disks_binary(300, 300, 4, 20, 0.3, seed=43)[0])
+    sq, nn = cuda_ctx.edt(torch.from_numpy(b).to(DEV))
+    assert sq.cpu().numpy().max() > 0
+
+
 def test_empty_images_are_rejected(cuda_ctx):
     for shape in ((0, 5), (5, 0), (0, 0)):
         a = torch.zeros(shape, dtype=torch.uint8, device=DEV)
