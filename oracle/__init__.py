@@ -51,6 +51,7 @@ def _load():
         lib.oracle_edt_policy.argtypes = [i32, i32, vp, i32, vp, vp, i64p, i32,
                                           ctypes.c_uint64]
         lib.oracle_edt_exact.argtypes = [i32, i32, vp, i32, vp]
+        lib.oracle_gdt.argtypes = [i32, i32, vp, vp, vp, i64p]
         for f in ("oracle_fh_i32", "oracle_fh_u8", "oracle_edt",
                   "oracle_edt_policy", "oracle_edt_exact"):
             getattr(lib, f).restype = ctypes.c_int
@@ -122,6 +123,52 @@ def edt_exact(binary: np.ndarray, feature_nonzero: bool = False) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- definitions
+
+def gdt(mask: np.ndarray, seeds: np.ndarray, stats: dict | None = None) -> np.ndarray:
+    """Geodesic (shortest-path) distance through free pixels (mask != 0)
+    from sources (free pixels with seeds != 0); 8 moves, cost 5 straight and
+    7 diagonal; INT32_MAX for obstacles and unreachable pixels (Section 1's
+    shortest paths on a grid with obstacles; Dijkstra's algorithm)."""
+    lib = _load()
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    s = np.ascontiguousarray(seeds, dtype=np.uint8)
+    assert m.shape == s.shape and m.ndim == 2
+    h, w = m.shape
+    out = np.empty((h, w), np.int32)
+    st = np.zeros(2, np.int64)
+    rc = lib.oracle_gdt(h, w, _ptr(m), _ptr(s), _ptr(out), st.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if rc != 0:
+        raise MemoryError("oracle_gdt")
+    if stats is not None:
+        stats.update(pops=int(st[0]), improvements=int(st[1]))
+    return out
+
+
+def gdt_bellman_ford(mask: np.ndarray, seeds: np.ndarray) -> np.ndarray:
+    """The same distances by plain relaxation to a fixpoint (every free pixel
+    takes the least neighbour distance plus the step cost, repeated until
+    nothing changes): a brute-force check of gdt on small grids."""
+    m = np.asarray(mask) != 0
+    INF = np.iinfo(np.int64).max // 4
+    d = np.where(m & (np.asarray(seeds) != 0), 0, INF).astype(np.int64)
+    h, w = d.shape
+    while True:
+        best = d.copy()
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if dy == 0 and dx == 0:
+                    continue
+                cost = 7 if dy and dx else 5
+                sh = np.full_like(d, INF)
+                sh[max(dy, 0):h + min(dy, 0), max(dx, 0):w + min(dx, 0)] = \
+                    d[max(-dy, 0):h + min(-dy, 0), max(-dx, 0):w + min(-dx, 0)]
+                best = np.minimum(best, np.where(sh < INF, sh + cost, INF))
+        best = np.where(m, best, INF)
+        if np.array_equal(best, d):
+            break
+        d = best
+    return np.where(d >= INF, np.iinfo(np.int32).max, d).astype(np.int32)
+
 
 def _neighbour_max(J: np.ndarray, conn: int) -> np.ndarray:
     """max over N_G(p) u {p}; pixels outside the image do not exist."""

@@ -19,6 +19,9 @@
  *                                 Roerdink and Hesselink (2000); used to count
  *                                 where Algorithm 3 departs from the exact
  *                                 distance (Section 2.2, Figure 3).
+ *   oracle_gdt                    Shortest-path (geodesic) distance on a grid
+ *                                 with obstacles, one of the IWPP uses named
+ *                                 in Section 1, by Dijkstra's algorithm.
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *   - pixels outside the image do not exist (no padding, no wrap-around);
@@ -337,3 +340,88 @@ int oracle_edt_exact(int h, int w, const uint8_t *bin, int feature_nonzero,
     free(g); free(s); free(t);
     return 0;
 }
+
+/* ------------------------------------ shortest paths on a grid (Section 1) */
+
+/*
+ * Geodesic distance from source pixels through free pixels, avoiding
+ * obstacles: the shortest-path computation on a grid with obstacles that
+ * Section 1 names as an instance of the IWPP.  The grid and the step costs
+ * are this build's choice (the paper gives none):
+ *   free(p)   = mask[p] != 0 (0 = obstacle);
+ *   sources   = free pixels with seed[p] != 0;
+ *   moves     = to any free 8-neighbour, cost 5 (horizontal or vertical)
+ *               or 7 (diagonal) -- the 5-7 chamfer weights;
+ *   dist[p]   = least total cost of a path from any source to p;
+ *               INT32_MAX for obstacles and unreachable pixels.
+ * Computed by Dijkstra's algorithm with a binary heap (lazy deletion: a
+ * popped entry whose key exceeds the current distance is skipped).
+ * stats (optional): [0] heap pops, [1] relaxations that improved a pixel.
+ */
+typedef struct { int64_t key; int64_t idx; } heap_item;
+
+static void heap_push(heap_item *hp, int64_t *n, int64_t key, int64_t idx) {
+    int64_t i = (*n)++;
+    while (i > 0) {
+        int64_t parent = (i - 1) / 2;
+        if (hp[parent].key <= key) break;
+        hp[i] = hp[parent];
+        i = parent;
+    }
+    hp[i].key = key;
+    hp[i].idx = idx;
+}
+
+static heap_item heap_pop(heap_item *hp, int64_t *n) {
+    heap_item top = hp[0], last = hp[--(*n)];
+    int64_t i = 0;
+    while (1) {
+        int64_t c = 2 * i + 1;
+        if (c >= *n) break;
+        if (c + 1 < *n && hp[c + 1].key < hp[c].key) c++;
+        if (last.key <= hp[c].key) break;
+        hp[i] = hp[c];
+        i = c;
+    }
+    if (*n > 0) hp[i] = last;
+    return top;
+}
+
+int oracle_gdt(int h, int w, const uint8_t *mask, const uint8_t *seed, int32_t *dist,
+               int64_t *stats) {
+    const int64_t n = (int64_t)h * w;
+    /* every improvement pushes one entry: at most 8 per pixel plus sources */
+    heap_item *hp = (heap_item *)malloc((size_t)(9 * n + 1) * sizeof(heap_item));
+    if (!hp) return -1;
+    int64_t hn = 0, pops = 0, relax = 0;
+    for (int64_t i = 0; i < n; i++) {
+        dist[i] = INT32_MAX;
+        if (mask[i] && seed[i]) {
+            dist[i] = 0;
+            heap_push(hp, &hn, 0, i);
+        }
+    }
+    while (hn > 0) {
+        heap_item it = heap_pop(hp, &hn);
+        pops++;
+        if (it.key > dist[it.idx]) continue; /* stale entry */
+        const int y = (int)(it.idx / w), x = (int)(it.idx % w);
+        for (int k = 0; k < 8; k++) {
+            const int qy = y + NB8[k][0], qx = x + NB8[k][1];
+            if (!inside(qy, qx, h, w)) continue;
+            const int64_t q = (int64_t)qy * w + qx;
+            if (!mask[q]) continue;
+            const int64_t cost = (NB8[k][0] != 0 && NB8[k][1] != 0) ? 7 : 5;
+            const int64_t nd = it.key + cost;
+            if (nd < dist[q]) {
+                dist[q] = (int32_t)nd;
+                heap_push(hp, &hn, nd, q);
+                relax++;
+            }
+        }
+    }
+    free(hp);
+    if (stats) { stats[0] = pops; stats[1] = relax; }
+    return 0;
+}
+
