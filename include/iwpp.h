@@ -182,6 +182,23 @@ int iwpp_edt_exact(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist,
                    int32_t *nearest, int flags, void *stream);
 
 /*
+ * Shortest paths on a grid with obstacles, which Section 1 names as a
+ * further instance of the IWPP, by the same tile-parallel wavefront.
+ * mask, seeds: IWPP_U8 images of one shape (pitches may differ); a pixel is
+ * free where mask != 0 (0 = obstacle) and a source where it is free and
+ * seeds != 0.  Paths move to any free 8-neighbour at cost 5 (horizontal or
+ * vertical) or 7 (diagonal): this build's choice of grid metric, the 5-7
+ * chamfer weights.  dist (dense h*w int32, device) receives each pixel's
+ * least path cost from any source: 0 at sources, INT32_MAX at obstacles
+ * and unreachable pixels.  Exact (integer costs; the least cost is unique).
+ * Limits: h*w < 2^31.  Not part of mixed job batches.
+ */
+int iwpp_geodesic(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image *seeds,
+                  int32_t *dist, void *stream);
+int iwpp_geodesic_async(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image *seeds,
+                        int32_t *dist, void *stream);
+
+/*
  * Batched entry points: n independent images in ONE persistent launch
  * (tiles of all images share one tile queue).  Arrays are host arrays of n
  * descriptors / pointers; the images themselves are on the device.

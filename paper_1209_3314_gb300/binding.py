@@ -86,6 +86,8 @@ SIGNATURES = {
     "iwpp_edt": (_i32, [_vp, ctypes.POINTER(Image), _vp, _vp, _i32, _vp]),
     "iwpp_edt_async": (_i32, [_vp, ctypes.POINTER(Image), _vp, _vp, _i32, _vp]),
     "iwpp_edt_exact": (_i32, [_vp, ctypes.POINTER(Image), _vp, _vp, _i32, _vp]),
+    "iwpp_geodesic": (_i32, [_vp, ctypes.POINTER(Image), ctypes.POINTER(Image), _vp, _vp]),
+    "iwpp_geodesic_async": (_i32, [_vp, ctypes.POINTER(Image), ctypes.POINTER(Image), _vp, _vp]),
     "iwpp_recon_batched": (_i32, [_vp, _i32, ctypes.POINTER(Image), ctypes.POINTER(Image), _i32,
                                   ctypes.POINTER(Image), _vp]),
     "iwpp_edt_batched": (_i32, [_vp, _i32, ctypes.POINTER(Image), ctypes.POINTER(_vp),
@@ -276,6 +278,23 @@ class Context:
         self._check(fn(self.h, ctypes.byref(b), ctypes.c_void_p(sqdist.data_ptr()),
                        ctypes.c_void_p(nearest.data_ptr()), flags, _stream_ptr(stream)))
         return sqdist, nearest
+
+    def geodesic(self, mask, seeds, dist=None, stream=None, sync: bool = True):
+        """Shortest-path distance through free pixels (mask != 0) from the
+        sources (free pixels with seeds != 0): uint8 CUDA tensors of one
+        shape.  8 moves, cost 5 straight / 7 diagonal.  Returns dist (int32;
+        INT32_MAX at obstacles and unreachable pixels)."""
+        torch = _torch()
+        h, w = mask.shape
+        if dist is None:
+            dist = torch.empty((h, w), dtype=torch.int32, device=mask.device)
+        if dist.dtype != torch.int32 or tuple(dist.shape) != (h, w) or not dist.is_contiguous() or not dist.is_cuda:
+            raise ValueError("dist must be a contiguous int32 CUDA tensor of the image shape")
+        m, s = image_of(mask), image_of(seeds)
+        fn = self.lib.iwpp_geodesic if sync else self.lib.iwpp_geodesic_async
+        self._check(fn(self.h, ctypes.byref(m), ctypes.byref(s), ctypes.c_void_p(dist.data_ptr()),
+                       _stream_ptr(stream)))
+        return dist
 
     def recon_batched(self, markers, masks, conn: int = 8, outs=None, stream=None):
         torch = _torch()

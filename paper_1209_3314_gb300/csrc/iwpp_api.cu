@@ -78,6 +78,7 @@ bool overlaps(const iwpp_image *a, const iwpp_image *b) {
 // the specialised kernel with the smallest shared-memory footprint.
 int pick_family(const std::vector<JobDesc> &jobs) {
     bool r8 = false, r32 = false, e = false;
+    if (!jobs.empty() && jobs[0].op == OP_GDT) return FAM_GDT;  // geodesic launches hold only geodesic jobs
     for (const JobDesc &j : jobs) {
         if (j.op == OP_EDT) e = true;
         else if (j.dtype == DT_U8) r8 = true;
@@ -130,6 +131,10 @@ bool make_map(CUtensorMap *m, const void *base, int dtype, int h, int w, int64_t
 
 void make_maps(JobDesc &d) {
     bool ok;
+    if (d.op == OP_GDT) {  // staged with plain loads
+        d.use_tma = 0;
+        return;
+    }
     if (d.op == OP_RECON) {
         ok = make_map(&d.tm[0], d.a, d.dtype, d.h, d.w, d.pa) && make_map(&d.tm[1], d.b, d.dtype, d.h, d.w, d.pb) &&
              make_map(&d.tm[2], d.out, d.dtype, d.h, d.w, d.po);
@@ -356,6 +361,36 @@ int check_edt(iwpp_ctx *ctx, const iwpp_image *bin, const int32_t *sq, const int
     return IWPP_OK;
 }
 
+int check_gdt(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image *seeds, const int32_t *dist) {
+    int rc;
+    if ((rc = check_image(ctx, mask, "mask")) || (rc = check_image(ctx, seeds, "seeds"))) return rc;
+    if (mask->dtype != IWPP_U8 || seeds->dtype != IWPP_U8)
+        return fail(ctx, IWPP_EINVAL, "geodesic distance: mask and seeds must be uint8");
+    if (mask->h != seeds->h || mask->w != seeds->w)
+        return fail(ctx, IWPP_EINVAL, "geodesic distance: mask and seeds must have the same shape");
+    if (!dist) return fail(ctx, IWPP_EINVAL, "null output pointer");
+    if ((int64_t)mask->h * mask->w >= ((int64_t)1 << 31))
+        return fail(ctx, IWPP_EINVAL, "geodesic distance limited to h*w < 2^31");
+    return IWPP_OK;
+}
+
+JobDesc gdt_job(const iwpp_image *mask, const iwpp_image *seeds, int32_t *dist) {
+    JobDesc d;
+    memset(&d, 0, sizeof d);
+    d.op = OP_GDT;
+    d.dtype = DT_U8;
+    d.conn = 8;
+    d.h = mask->h;
+    d.w = mask->w;
+    d.a = mask->data;
+    d.b = seeds->data;
+    d.out = dist;
+    d.pa = mask->pitch;
+    d.pb = seeds->pitch;
+    d.po = mask->w;
+    return d;
+}
+
 JobDesc edt_job(const iwpp_image *bin, int32_t *sq, int32_t *nn, int flags) {
     JobDesc d;
     memset(&d, 0, sizeof d);
@@ -558,6 +593,23 @@ int iwpp_edt(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist, int32_t *
     if (rc) return rc;
     std::vector<JobDesc> jobs{edt_job(binary, sqdist, nearest, flags)};
     return run(ctx, jobs, (cudaStream_t)stream, true);
+}
+
+int iwpp_geodesic(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image *seeds, int32_t *dist, void *stream) {
+    if (!ctx) return IWPP_EINVAL;
+    int rc = check_gdt(ctx, mask, seeds, dist);
+    if (rc) return rc;
+    std::vector<JobDesc> jobs{gdt_job(mask, seeds, dist)};
+    return run(ctx, jobs, (cudaStream_t)stream, true);
+}
+
+int iwpp_geodesic_async(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image *seeds, int32_t *dist,
+                        void *stream) {
+    if (!ctx) return IWPP_EINVAL;
+    int rc = check_gdt(ctx, mask, seeds, dist);
+    if (rc) return rc;
+    std::vector<JobDesc> jobs{gdt_job(mask, seeds, dist)};
+    return run(ctx, jobs, (cudaStream_t)stream, false);
 }
 
 int iwpp_edt_exact(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist, int32_t *nearest, int flags,

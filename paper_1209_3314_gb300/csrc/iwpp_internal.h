@@ -10,11 +10,11 @@
 
 namespace iwpp {
 
-enum : int { OP_RECON = 0, OP_EDT = 1 };
+enum : int { OP_RECON = 0, OP_EDT = 1, OP_GDT = 2 };
 enum : int { DT_U8 = 0, DT_I32 = 1 };
 
 // kernel families (one persistent-kernel instantiation each)
-enum : int { FAM_RECON_U8 = 0, FAM_RECON_I32 = 1, FAM_EDT = 2, FAM_MIXED = 3, FAM_COUNT = 4 };
+enum : int { FAM_RECON_U8 = 0, FAM_RECON_I32 = 1, FAM_EDT = 2, FAM_MIXED = 3, FAM_GDT = 4, FAM_COUNT = 5 };
 
 constexpr int TILE = 64;  // tile side in pixels
 

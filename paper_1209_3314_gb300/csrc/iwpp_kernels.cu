@@ -89,12 +89,18 @@ static_assert(
               "queues must fit the staging union");
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
+// geodesic distance: D as the int32 box layout (stride 72, cell (r, c) at
+// word r*72 + c + 3), the mask as a uint8 box (stride 96, cell (r, c) at
+// byte r*96 + c + 15), then the block queues
+constexpr int QCAP_G = 1024;
+constexpr int G_D = HDR_BYTES, G_M = G_D + BI32_PAD, G_U = G_M + BU8_PAD;
+constexpr int G_BYTES = G_U + 2 * QCAP_G * 2;
 constexpr int FAM_SMEM[FAM_COUNT] = {RU8_BYTES, RI32_BYTES, E_BYTES,
-                                     cmax(cmax(RU8_BYTES, RI32_BYTES), E_BYTES)};
-constexpr int FAM_NT[FAM_COUNT] = {64, 64, 128, 128};
+                                     cmax(cmax(RU8_BYTES, RI32_BYTES), E_BYTES), G_BYTES};
+constexpr int FAM_NT[FAM_COUNT] = {64, 64, 128, 128, 64};
 // resident CTAs per SM that each family's shared memory allows; the
 // register budget is sized for them
-constexpr int FAM_MINB[FAM_COUNT] = {14, 5, 8, 5};
+constexpr int FAM_MINB[FAM_COUNT] = {14, 5, 8, 5, 7};
 
 // neighbourhood offsets (dy, dx); 8-connected: the first 4 are N+ (raster)
 __device__ __forceinline__ int nb_dy(int conn, int k) {
@@ -1359,6 +1365,257 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
 }
 
 // =====================================================================
+// Shortest paths on a grid with obstacles (Section 1's further IWPP use)
+// =====================================================================
+//
+// D(p) = least cost of a path from a source to p through free pixels, with
+// 8 moves costing 5 (straight) or 7 (diagonal).  Wavefront element: a pixel
+// whose D may lower a free neighbour; update: D(q) = D(p) + w (atomicMin).
+// Sweeps: Algorithm 2's raster / anti-raster passes with min-plus in place
+// of max-min.  Obstacles and pixels outside the image keep GD_INF.
+
+constexpr int GD_INF = 0x3FFFFFFF;  // > any path cost; GD_INF + 7 still fits
+
+__device__ __forceinline__ int gcell(int r, int c) { return r * BI32_W + c + 3; }
+__device__ __forceinline__ int gmask(int r, int c) { return r * BU8_W + c + 15; }
+__device__ __forceinline__ int gstep(int n) { return (nb_dy(8, n) != 0 && nb_dx(8, n) != 0) ? 7 : 5; }
+
+template <int DIR>
+__device__ __forceinline__ bool gdt_row_pass(int *__restrict__ D, const uint8_t *__restrict__ M, int r) {
+    const int base = gcell(r, 0), mb = gmask(r, 0);
+    int run = D[base + (DIR > 0 ? 0 : TS + 1)];
+    bool ch = false;
+#pragma unroll 4
+    for (int s = 1; s <= TS; ++s) {
+        const int c = DIR > 0 ? s : TS + 1 - s;
+        const int o = D[base + c];
+        const int v = M[mb + c] ? min(o, run + 5) : o;
+        if (v != o) { D[base + c] = v; ch = true; }
+        run = v;
+    }
+    return ch;
+}
+
+// column pass; the diagonal neighbours of the previous row are read from
+// shared memory (old or new: both are valid upper bounds)
+template <int DIR>
+__device__ __forceinline__ bool gdt_column_pass(int *__restrict__ D, const uint8_t *__restrict__ M, int t) {
+    const int c = t + 1;
+    const int r0 = DIR > 0 ? 0 : RR - 1;
+    int up = D[gcell(r0, c)];
+    bool ch = false;
+#pragma unroll 4
+    for (int s = 1; s <= TS; ++s) {
+        const int r = DIR > 0 ? s : RR - 1 - s;
+        const int i = gcell(r, c), ip = i - DIR * BI32_W;
+        const int o = D[i];
+        int v = o;
+        if (M[gmask(r, c)]) v = min(o, min(up + 5, min(D[ip - 1], D[ip + 1]) + 7));
+        if (v != o) { D[i] = v; ch = true; }
+        up = v;
+    }
+    return ch;
+}
+
+__device__ bool gdt_sweep_set(int *D, const uint8_t *M) {
+    const int t = threadIdx.x;
+    bool ch = false;
+    if (t < TS) {
+        ch |= gdt_row_pass<+1>(D, M, t + 1);
+        ch |= gdt_row_pass<-1>(D, M, t + 1);
+    }
+    __syncthreads();
+    if (t < TS) {
+        ch |= gdt_column_pass<+1>(D, M, t);
+        ch |= gdt_column_pass<-1>(D, M, t);
+    }
+    return __syncthreads_or(ch) != 0;
+}
+
+// One relaxation step over the interior (each free pixel takes the least
+// neighbour D plus step cost); the pixels it lowers are queued.  Afterwards
+// every pixel that can still lower a neighbour is queued (a pixel that did
+// not change was seen by each neighbour during the step).
+template <int NT>
+__device__ unsigned gdt_dilate_seed(int *D, const uint8_t *M, const RQ &q, const int *off) {
+    unsigned pushed = 0;
+    for (int base = 0; base < TS * TS; base += NT) {
+        const int k = base + threadIdx.x;
+        unsigned m = 0;
+        int i = 0;
+        if (k < TS * TS) {
+            const int r = k / TS + 1, c = k - (k / TS) * TS + 1;
+            i = gcell(r, c);
+            if (M[gmask(r, c)]) {
+                const int o = D[i];
+                int v = o;
+#pragma unroll
+                for (int n = 0; n < 8; ++n) v = min(v, D[i + off[n]] + gstep(n));
+                if (v < o) {
+                    D[i] = v;
+                    m = 1u << 8;
+                }
+            }
+        }
+        pushed += warp_enqueue(m, i, off, q);
+    }
+    return pushed;
+}
+
+// later visits: halo pixels that can lower a free interior neighbour
+template <int NT>
+__device__ unsigned gdt_halo_seed(int *D, const uint8_t *M, const RQ &q, const int *off) {
+    unsigned pushed = 0;
+    for (int base = 0; base < 4 * (TS + 1); base += NT) {
+        const int k = base + threadIdx.x;
+        unsigned m = 0;
+        int i = 0;
+        if (k < 4 * (TS + 1)) {
+            int r, c;
+            halo_cell(k, r, c);
+            i = gcell(r, c);
+            const int dp = D[i];
+#pragma unroll
+            for (int n = 0; n < 8; ++n) {
+                const int rr = r + nb_dy(8, n), cc = c + nb_dx(8, n);
+                if (rr >= 1 && rr <= TS && cc >= 1 && cc <= TS && M[gmask(rr, cc)] &&
+                    dp + gstep(n) < D[i + off[n]])
+                    m = 1u << 8;
+            }
+        }
+        pushed += warp_enqueue(m, i, off, q);
+    }
+    return pushed;
+}
+
+template <int NT>
+__device__ bool gdt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, uint32_t &phase,
+                          unsigned long long deadline) {
+    (void)phase;
+    int *hdr = (int *)sm;
+    int *D = (int *)(sm + G_D);
+    uint8_t *M = (uint8_t *)(sm + G_M);
+    uint16_t *Q0 = (uint16_t *)(sm + G_U), *Q1 = Q0 + QCAP_G;
+    const int tid = threadIdx.x;
+    const int lt = gt - jd->tile_base, tx = lt % jd->tiles_x, ty = lt / jd->tiles_x;
+    const int x0 = tx * TS, y0 = ty * TS;
+    const uint8_t *mk = (const uint8_t *)jd->a, *sd = (const uint8_t *)jd->b;
+    int *out = (int *)jd->out;
+
+    PhaseClock pc;
+    pc.start();
+    load_sources(ka, jd, tx, ty, hdr);
+    begin_visit(hdr);
+    make_offsets<8, BI32_W>(hdr);
+    // 1. stage the mask box (zero, i.e. obstacle, outside the image) and D:
+    //    visited regions from the current result, the others from the
+    //    sources (0 at a free source, GD_INF elsewhere)
+    stage_plain<uint8_t, BU8_W>(M, mk, jd->pa, jd->h, jd->w, x0 - 16, y0 - 1, NT);
+    __syncthreads();
+    const bool first = hdr[H_SRC + 4] == 0;
+#pragma unroll 4
+    for (int i = tid; i < RR * RR; i += NT) {
+        const int r = i / RR, c = i - r * RR;
+        const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+        int v = GD_INF;
+        if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
+            if (hdr[H_SRC + region(r) * 3 + region(c)] == 1) {
+                const int o = __ldcg(out + (int64_t)gy * jd->po + gx);
+                v = o < GD_INF ? o : GD_INF;
+            } else if (M[gmask(r, c)] && __ldcg(sd + (int64_t)gy * jd->pb + gx)) {
+                v = 0;
+            }
+        }
+        D[gcell(r, c)] = v;
+    }
+    __syncthreads();
+    pc.mark(hdr, 0);
+    const int *off = hdr + H_OFF;
+
+    // 2. seeds: sweep sets then one relaxation step (first visit, or a
+    //    later visit whose halo changed in many places); else halo seeds
+    uint16_t *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
+    const int qcap = (ka.queue_mode & 2) ? 0 : QCAP_G;
+    RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, qcap, ka.spill_cap, ka.queue_mode & 1};
+    auto sweeps_then_seed = [&]() -> unsigned {
+        bool changed = true;
+        for (int s = 0; s < ka.sweeps && changed; ++s) changed = gdt_sweep_set(D, M);
+        if (!changed && ka.sweeps > 0) return 0u;
+        return gdt_dilate_seed<NT>(D, M, q0, off);
+    };
+    unsigned seeds;
+    if (first) {
+        seeds = sweeps_then_seed();
+    } else {
+        seeds = gdt_halo_seed<NT>(D, M, q0, off);
+        __syncthreads();
+        if (hdr[H_CNT0] > ka.revisit_sweep_min) {
+            __syncthreads();
+            if (tid == 0) { hdr[H_CNT0] = 0; hdr[H_RESCAN] = 0; }
+            __syncthreads();
+            seeds = sweeps_then_seed();
+        }
+    }
+    if ((tid & 31) == 0) atomicAdd(hdr + H_SEEDS, (int)seeds);
+    pc.mark(hdr, 1);
+
+    // 3. propagation rounds (atomicMin updates of free interior pixels)
+    auto proc = [&](int p, int n) -> bool {
+        const int pr = p / BI32_W, pcol = p - pr * BI32_W - 3;
+        const int rr = pr + nb_dy(8, n), cc = pcol + nb_dx(8, n);
+        if (rr < 1 || rr > TS || cc < 1 || cc > TS || !M[gmask(rr, cc)]) return false;
+        const int cand = ((volatile int *)D)[p] + gstep(n);
+        return atomicMin(D + p + off[n], cand) > cand;
+    };
+    auto rescan = [&](const RQ &q) -> unsigned { return gdt_dilate_seed<NT>(D, M, q, off); };
+    run_rounds<NT, 8>(hdr, Q0, Q1, qcap, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl,
+                      ka.queue_mode & 1);
+    __syncthreads();
+    pc.mark(hdr, 2);
+
+    // 4. store the interior (unreachable: INT32_MAX)
+    load_sources(ka, jd, tx, ty, hdr);
+    for (int i = tid; i < TS * TS; i += NT) {
+        const int r = i / TS, c = i - r * TS;
+        const int gy = y0 + r, gx = x0 + c;
+        if (gy >= jd->h || gx >= jd->w) continue;
+        const int v = D[gcell(r + 1, c + 1)];
+        out[(int64_t)gy * jd->po + gx] = v >= GD_INF ? INT_MAX : v;
+    }
+    __syncthreads();
+    publish_tile(ka, gt, hdr);
+
+    // 5. border test: can an interior pixel lower a free halo pixel's
+    //    current value (its tile's result, or its source value)?
+    for (int k = tid; k < 4 * (TS + 1); k += NT) {
+        int r, c;
+        halo_cell(k, r, c);
+        const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+        if (gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w || !M[gmask(r, c)]) continue;
+        const int reg = region(r) * 3 + region(c);
+        int cur;
+        if (hdr[H_SRC + reg] == 1) {
+            const int o = __ldcg(out + (int64_t)gy * jd->po + gx);
+            cur = o < GD_INF ? o : GD_INF;
+        } else {
+            cur = __ldcg(sd + (int64_t)gy * jd->pb + gx) ? 0 : GD_INF;
+        }
+        bool need = false;
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            const int pr = r + nb_dy(8, n), pcc = c + nb_dx(8, n);
+            if (pr < 1 || pr > TS || pcc < 1 || pcc > TS) continue;
+            if (D[gcell(pr, pcc)] + gstep(n) < cur) need = true;
+        }
+        if (need) hdr[H_FLAG + reg] = 1;
+    }
+    __syncthreads();
+    finish_tile(ka, jd, gt, tx, ty, hdr);
+    pc.mark(hdr, 3);
+    return true;
+}
+
+// =====================================================================
 // kernels
 // =====================================================================
 
@@ -1402,7 +1659,12 @@ __global__ void __launch_bounds__(FAM_NT[FAM], FAM_MINB[FAM]) persistent_kernel(
                                        : recon_i32_visit<4, NT>(ka, jd, t, smem, phase, deadline);
             }
         } else {
-            if constexpr (FAM == FAM_EDT || FAM == FAM_MIXED) ok = edt_visit<NT>(ka, jd, t, smem, phase, deadline);
+            if constexpr (FAM == FAM_EDT || FAM == FAM_MIXED) {
+                if (jd->op == OP_EDT) ok = edt_visit<NT>(ka, jd, t, smem, phase, deadline);
+            }
+            if constexpr (FAM == FAM_GDT) {
+                if (jd->op == OP_GDT) ok = gdt_visit<NT>(ka, jd, t, smem, phase, deadline);
+            }
         }
         if (!ok) break;  // timeout raised; the host reports it
         if (threadIdx.x == 0) {
@@ -1518,6 +1780,7 @@ cudaError_t family_occupancy(int fam, int *n) {
         case FAM_RECON_I32: return occ<FAM_RECON_I32>(n);
         case FAM_EDT: return occ<FAM_EDT>(n);
         case FAM_MIXED: return occ<FAM_MIXED>(n);
+        case FAM_GDT: return occ<FAM_GDT>(n);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1545,6 +1808,7 @@ cudaError_t launch_persistent(const KArgs &ka, int fam, int grid, cudaStream_t s
         case FAM_RECON_I32: launch_fam<FAM_RECON_I32>(ka, grid, s); break;
         case FAM_EDT: launch_fam<FAM_EDT>(ka, grid, s); break;
         case FAM_MIXED: launch_fam<FAM_MIXED>(ka, grid, s); break;
+        case FAM_GDT: launch_fam<FAM_GDT>(ka, grid, s); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
