@@ -484,6 +484,54 @@ def bench_coverage(ctx, dev, d_marker, d_mask, side, reps=3):
             "runs": rows_out}
 
 
+def bench_geodesic(ctx, dev, side, reps=3):
+    """Shortest paths on a grid with obstacles (iwpp_geodesic): a side x side
+    field with 30 % random obstacles and 256 random sources, and a
+    serpentine maze of side/8 whose single corridor crosses every tile row
+    many times (a sequential worst case for any wavefront).  Per-call
+    CUDA-event times (median)."""
+    import statistics
+
+    import numpy as np
+    import torch
+
+    rng = np.random.default_rng(5000)
+    m = (rng.random((side, side), dtype=np.float32) >= 0.3).astype(np.uint8)
+    s = np.zeros((side, side), np.uint8)
+    s[rng.integers(0, side, 256), rng.integers(0, side, 256)] = 1
+    ms = side // 8
+    maze = np.ones((ms, ms), np.uint8)
+    for k, r in enumerate(range(6, ms, 6)):
+        maze[r, :] = 0
+        if k % 2 == 0:
+            maze[r, ms - 2:] = 1
+        else:
+            maze[r, :2] = 1
+    mseed = np.zeros((ms, ms), np.uint8)
+    mseed[0, 0] = 1
+    st = torch.cuda.current_stream(dev)
+    res = {}
+    for name, (mk, sd) in (("random_30pct", (m, s)), ("serpentine_maze", (maze, mseed))):
+        dm, ds = torch.from_numpy(mk).to(dev), torch.from_numpy(sd).to(dev)
+        dist = torch.empty(dm.shape, dtype=torch.int32, device=dev)
+        ctx.geodesic(dm, ds, dist=dist)
+        ctx.stats_reset()
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            ctx.geodesic(dm, ds, dist=dist, sync=False)
+            b.record(st)
+            ctx.sync()
+            times.append(a.elapsed_time(b))
+        q = ctx.stats()
+        ms_ = statistics.median(times)
+        res[name] = {"side": int(dm.shape[0]), "ms": round(ms_, 3), "mpx_s": round(dm.numel() / ms_ / 1e3, 1),
+                     "tiles_per_call": q["tiles_processed"] // reps}
+        del dm, ds, dist
+    return res
+
+
 def run_gpu(args, ws, rank, local):
     import numpy as np
     import torch
@@ -660,6 +708,9 @@ def run_gpu(args, ws, rank, local):
     coverage = None
     if rank == 0 and not args.skip_coverage:
         coverage = bench_coverage(ctx, dev, d_marker, d_mask, side)
+    geodesic = None
+    if rank == 0 and not args.skip_geodesic:
+        geodesic = bench_geodesic(ctx, dev, side)
     exact = None
     if rank == 0 and not args.skip_exact:
         exact = bench_edt_exact(ctx, dev, d_bin, npx)
@@ -702,6 +753,7 @@ def run_gpu(args, ws, rank, local):
             "queue_ablation": ablation,
             "edt_exact": exact,
             "coverage": coverage,
+            "geodesic": geodesic,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_val, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3), "check": ok},
@@ -728,6 +780,7 @@ def main():
     ap.add_argument("--skip-ablation", action="store_true")
     ap.add_argument("--skip-exact", action="store_true")
     ap.add_argument("--skip-coverage", action="store_true")
+    ap.add_argument("--skip-geodesic", action="store_true")
     ap.add_argument("--batch-images", type=int, default=512)
     ap.add_argument("--serve-rates", default="200,500,1000,2000")
     ap.add_argument("--serve-duration", type=float, default=1.0)

@@ -118,7 +118,9 @@ typedef struct {
                                 one claim waits until timeout_ms runs out and
                                 the call returns IWPP_ETIMEOUT (no fault, no
                                 hang: every device wait is bounded)           */
-    int32_t reserved[2];
+    int32_t gdt_sweeps;      /* shortest paths: sweep sets per bulk visit
+                                (obstacles bend the paths, so more sets pay)  */
+    int32_t reserved[1];
 } iwpp_options;
 
 /* Creates a context on `device`.  hbm_budget_bytes bounds the workspace the

@@ -131,8 +131,10 @@ bool make_map(CUtensorMap *m, const void *base, int dtype, int h, int w, int64_t
 
 void make_maps(JobDesc &d) {
     bool ok;
-    if (d.op == OP_GDT) {  // staged with plain loads
-        d.use_tma = 0;
+    if (d.op == OP_GDT) {  // mask, sources, current result
+        d.use_tma = make_map(&d.tm[0], d.a, DT_U8, d.h, d.w, d.pa) &&
+                    make_map(&d.tm[1], d.b, DT_U8, d.h, d.w, d.pb) &&
+                    make_map(&d.tm[2], d.out, DT_I32, d.h, d.w, d.po);
         return;
     }
     if (d.op == OP_RECON) {
@@ -246,6 +248,7 @@ int prepare(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, const iwpp_options &opt, 
     ka.revisit_sweeps = opt.revisit_sweeps < 0 ? opt.sweeps : opt.revisit_sweeps;
     ka.queue_mode = opt.queue_mode;
     ka.test_empty_slot = opt.test_empty_slot;
+    ka.gdt_sweeps = opt.gdt_sweeps;
     ka.timeout_ns = (unsigned long long)opt.timeout_ms * 1000000ull;
     return IWPP_OK;
 }
@@ -511,6 +514,7 @@ int iwpp_ctx_create(iwpp_ctx **out, int device, size_t hbm_budget_bytes) {
     ctx->opt.edt_sweeps = 2;
     ctx->opt.edt_revisit_sweep_min = 64;
     ctx->opt.revisit_sweeps = -1;
+    ctx->opt.gdt_sweeps = 8;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&ctx->ctl, sizeof(Control)) != cudaSuccess ||
@@ -554,7 +558,7 @@ int iwpp_set_options(iwpp_ctx *ctx, const iwpp_options *o) {
         o->timeout_ms < 1 || o->timeout_ms > 600000 || o->timing < 0 || o->timing > 1 ||
         o->revisit_sweep_min < 0 || o->edt_sweeps < 0 || o->edt_sweeps > 64 || o->edt_revisit_sweep_min < 0 ||
         o->revisit_sweeps < -1 || o->revisit_sweeps > 64 || o->queue_mode < 0 || o->queue_mode > 3 ||
-        o->test_empty_slot < 0 || o->test_empty_slot > 1)
+        o->test_empty_slot < 0 || o->test_empty_slot > 1 || o->gdt_sweeps < 0 || o->gdt_sweeps > 64)
         return fail(ctx, IWPP_EINVAL, "option out of range");
     ctx->opt = *o;
     return IWPP_OK;

@@ -55,6 +55,7 @@ struct alignas(64) KArgs {
     int revisit_sweeps;   // reconstruction: sweep sets on a later visit
     int queue_mode;       // queue ablation: bit 0 per-thread atomics, bit 1 global-only
     int test_empty_slot;  // timeout-path tests: initial queue slot 0 left unfilled
+    int gdt_sweeps;       // shortest paths: sweep sets per bulk visit
     unsigned long long timeout_ns;
 };
 

@@ -91,10 +91,13 @@ static_assert(
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 // geodesic distance: D as the int32 box layout (stride 72, cell (r, c) at
 // word r*72 + c + 3), the mask as a uint8 box (stride 96, cell (r, c) at
-// byte r*96 + c + 15), then the block queues
+// byte r*96 + c + 15), then the sources' uint8 box in a union with the
+// block queues (sized so that 7 CTAs fit an SM)
 constexpr int QCAP_G = 1024;
-constexpr int G_D = HDR_BYTES, G_M = G_D + BI32_PAD, G_U = G_M + BU8_PAD;
-constexpr int G_BYTES = G_U + 2 * QCAP_G * 2;
+constexpr int G_D = HDR_BYTES, G_M = G_D + BI32_PAD, G_U = 25984;
+constexpr int G_BYTES = G_U + BU8_BYTES;
+static_assert(G_M + BU8_BYTES <= G_U && G_U % 128 == 0 && G_M % 128 == 0 && 2 * QCAP_G * 2 <= BU8_BYTES,
+              "geodesic layout");
 constexpr int FAM_SMEM[FAM_COUNT] = {RU8_BYTES, RI32_BYTES, E_BYTES,
                                      cmax(cmax(RU8_BYTES, RI32_BYTES), E_BYTES), G_BYTES};
 constexpr int FAM_NT[FAM_COUNT] = {64, 64, 128, 128, 64};
@@ -1491,8 +1494,8 @@ __device__ unsigned gdt_halo_seed(int *D, const uint8_t *M, const RQ &q, const i
 template <int NT>
 __device__ bool gdt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, uint32_t &phase,
                           unsigned long long deadline) {
-    (void)phase;
     int *hdr = (int *)sm;
+    uint64_t *bar = (uint64_t *)(sm + 256);
     int *D = (int *)(sm + G_D);
     uint8_t *M = (uint8_t *)(sm + G_M);
     uint16_t *Q0 = (uint16_t *)(sm + G_U), *Q1 = Q0 + QCAP_G;
@@ -1507,22 +1510,43 @@ __device__ bool gdt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     load_sources(ka, jd, tx, ty, hdr);
     begin_visit(hdr);
     make_offsets<8, BI32_W>(hdr);
-    // 1. stage the mask box (zero, i.e. obstacle, outside the image) and D:
-    //    visited regions from the current result, the others from the
-    //    sources (0 at a free source, GD_INF elsewhere)
-    stage_plain<uint8_t, BU8_W>(M, mk, jd->pa, jd->h, jd->w, x0 - 16, y0 - 1, NT);
+    // 1. stage the mask box (zero, i.e. obstacle, outside the image), the
+    //    current result's box (visited regions) and the sources' box
+    //    (unvisited regions: 0 at a free source, GD_INF elsewhere)
     __syncthreads();
     const bool first = hdr[H_SRC + 4] == 0;
-#pragma unroll 4
+    uint8_t *SB = (uint8_t *)(sm + G_U);
+    int need_s = 0, need_o = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        need_s |= hdr[H_SRC + k] == 0;
+        need_o |= hdr[H_SRC + k] == 1;
+    }
+    if (jd->use_tma) {
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, BU8_BYTES * (1 + need_s) + need_o * BI32_BYTES);
+            tma_load_2d(M, &jd->tm[0], x0 - 16, y0 - 1, bar);
+            if (need_s) tma_load_2d(SB, &jd->tm[1], x0 - 16, y0 - 1, bar);
+            if (need_o) tma_load_2d(D, &jd->tm[2], x0 - 4, y0 - 1, bar);
+        }
+        if (!wait_boxes(bar, phase, deadline, ka.ctl)) return false;
+    } else {
+        stage_plain<uint8_t, BU8_W>(M, mk, jd->pa, jd->h, jd->w, x0 - 16, y0 - 1, NT);
+        if (need_s) stage_plain<uint8_t, BU8_W>(SB, sd, jd->pb, jd->h, jd->w, x0 - 16, y0 - 1, NT);
+        if (need_o) stage_plain<int, BI32_W>(D, out, jd->po, jd->h, jd->w, x0 - 4, y0 - 1, NT);
+        __syncthreads();
+    }
     for (int i = tid; i < RR * RR; i += NT) {
         const int r = i / RR, c = i - r * RR;
         const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+        const int src = hdr[H_SRC + region(r) * 3 + region(c)];
         int v = GD_INF;
         if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
-            if (hdr[H_SRC + region(r) * 3 + region(c)] == 1) {
-                const int o = __ldcg(out + (int64_t)gy * jd->po + gx);
+            if (src == 1) {
+                const int o = D[gcell(r, c)];
                 v = o < GD_INF ? o : GD_INF;
-            } else if (M[gmask(r, c)] && __ldcg(sd + (int64_t)gy * jd->pb + gx)) {
+            } else if (M[gmask(r, c)] && SB[gmask(r, c)]) {
                 v = 0;
             }
         }
@@ -1539,8 +1563,8 @@ __device__ bool gdt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, qcap, ka.spill_cap, ka.queue_mode & 1};
     auto sweeps_then_seed = [&]() -> unsigned {
         bool changed = true;
-        for (int s = 0; s < ka.sweeps && changed; ++s) changed = gdt_sweep_set(D, M);
-        if (!changed && ka.sweeps > 0) return 0u;
+        for (int s = 0; s < ka.gdt_sweeps && changed; ++s) changed = gdt_sweep_set(D, M);
+        if (!changed && ka.gdt_sweeps > 0) return 0u;
         return gdt_dilate_seed<NT>(D, M, q0, off);
     };
     unsigned seeds;

@@ -101,12 +101,12 @@ def test_degenerate_cases(cuda_ctx):
     assert (d == IMAX).all()
 
 
-@pytest.mark.parametrize("sweeps,revisit_min,mode", [(0, 0, 0), (1, 0, 1), (3, 1 << 20, 2), (2, 16, 3)])
+@pytest.mark.parametrize("sweeps,revisit_min,mode", [(0, 0, 0), (1, 0, 1), (3, 1 << 20, 2), (12, 16, 3)])
 def test_settings_do_not_change_the_result(cuda_ctx, sweeps, revisit_min, mode):
     rng = np.random.default_rng(95)
     m, s = field(rng, 520, 610, 0.3, 4)
     ref = oracle.gdt(m, s)
-    got = run(cuda_ctx, m, s, sweeps=sweeps, revisit_sweep_min=revisit_min, queue_mode=mode)
+    got = run(cuda_ctx, m, s, gdt_sweeps=sweeps, revisit_sweep_min=revisit_min, queue_mode=mode)
     np.testing.assert_array_equal(got, ref)
 
 
