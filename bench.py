@@ -268,9 +268,11 @@ def bench_batched(ctx, dev, n, reps):
     return {"images": n, "pixels": px, "ms_per_batch": round(ms, 3), "imgs_s": round(n / ms * 1e3, 1),
             "mpx_s": round(px / ms / 1e3, 1), "one_per_launch_ms": round(base_ms, 3),
             "one_per_launch_imgs_s": round(n / base_ms * 1e3, 1), "speedup": round(base_ms / ms, 2),
-            "launch": "one persistent launch per batch, CUDA graph replay, autotuned",
+            "launch": ("one persistent launch per operation family (uint8 reconstruction, distance transform), "
+                       "back to back in one CUDA graph replay, autotuned" if tuned["batch_split"] else
+                       "one persistent launch for the whole batch, CUDA graph replay, autotuned"),
             "tuned": {k: tuned[k] for k in ("sweeps", "revisit_sweep_min", "edt_sweeps", "edt_revisit_sweep_min",
-                                                 "blocks_per_sm")}}
+                                                 "blocks_per_sm", "batch_split")}}
 
 
 def bench_served(ctx, dev, rates, duration, budget):

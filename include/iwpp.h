@@ -120,7 +120,12 @@ typedef struct {
                                 hang: every device wait is bounded)           */
     int32_t gdt_sweeps;      /* shortest paths: sweep sets per bulk visit
                                 (obstacles bend the paths, so more sets pay)  */
-    int32_t reserved[1];
+    int32_t batch_split;     /* batches of several operations: 0 one
+                                persistent launch with the kernel that runs
+                                them all; 1 one persistent launch per
+                                operation family, back to back on the stream
+                                (each with its smaller, faster kernel; the
+                                default); the autotuner tries both            */
 } iwpp_options;
 
 /* Creates a context on `device`.  hbm_budget_bytes bounds the workspace the

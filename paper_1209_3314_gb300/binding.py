@@ -51,7 +51,7 @@ class Options(ctypes.Structure):
                 ("revisit_sweep_min", ctypes.c_int32), ("edt_sweeps", ctypes.c_int32),
                 ("edt_revisit_sweep_min", ctypes.c_int32), ("revisit_sweeps", ctypes.c_int32),
                 ("queue_mode", ctypes.c_int32), ("test_empty_slot", ctypes.c_int32),
-                ("gdt_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("gdt_sweeps", ctypes.c_int32), ("batch_split", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):

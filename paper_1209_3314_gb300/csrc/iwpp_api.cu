@@ -284,10 +284,58 @@ int enqueue(iwpp_ctx *ctx, const Prepared &P, int max_relaunch, cudaStream_t st,
     return IWPP_OK;
 }
 
+// The launch groups of a batch: all jobs together, or (batch_split) one
+// group per operation family -- uint8 reconstruction, int32
+// reconstruction, distance transform, shortest paths -- in that order.
+std::vector<std::vector<JobDesc>> launch_groups(const std::vector<JobDesc> &jobs, int split) {
+    std::vector<std::vector<JobDesc>> g;
+    if (!split) {
+        g.push_back(jobs);
+        return g;
+    }
+    std::vector<JobDesc> by[4];
+    for (const JobDesc &j : jobs) {
+        const int k = j.op == OP_RECON ? (j.dtype == DT_U8 ? 0 : 1) : (j.op == OP_EDT ? 2 : 3);
+        by[k].push_back(j);
+    }
+    for (auto &v : by)
+        if (!v.empty()) g.push_back(v);
+    return g;
+}
+
 // Runs (or enqueues) the whole launch sequence for `jobs` on the context's
-// workspace.
+// workspace: one sequence per launch group, back to back on the stream
+// (they share the status block; its error bits accumulate).
 int run(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, cudaStream_t st, bool sync) {
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    std::vector<std::vector<JobDesc>> groups = launch_groups(jobs, ctx->opt.batch_split);
+    if (groups.size() > 1) {
+        std::vector<Prepared> Ps(groups.size());
+        std::vector<size_t> offs(groups.size());
+        size_t total = 0;
+        for (size_t k = 0; k < groups.size(); ++k) {
+            int rc = prepare(ctx, groups[k], ctx->opt, Ps[k]);
+            if (rc) return rc;
+            offs[k] = total;
+            total += align_up(Ps[k].ws_bytes, 256);
+        }
+        int rc = ensure_ws(ctx, total, st);
+        if (rc) return rc;
+        for (size_t k = 0; k < groups.size(); ++k) {
+            char *ws = (char *)ctx->ws + offs[k];
+            bind_workspace(Ps[k], ws, ctx->ctl);
+            if (groups[k].size() > 1)
+                CK(cudaMemcpyAsync(ws + Ps[k].o_jobs, groups[k].data(), groups[k].size() * sizeof(JobDesc),
+                                   cudaMemcpyHostToDevice, st),
+                   "job table upload");
+            if ((rc = enqueue(ctx, Ps[k], ctx->opt.max_relaunch, st, nullptr, nullptr))) return rc;
+            ctx->launches += 3 + 3 * (uint64_t)ctx->opt.max_relaunch;
+            ctx->tiles_initial += (uint64_t)Ps[k].ntiles;
+        }
+        ctx->calls += 1;
+        if (!sync) return IWPP_OK;
+        return iwpp_sync(ctx, st);
+    }
     Prepared P;
     int rc = prepare(ctx, jobs, ctx->opt, P);
     if (rc) return rc;
@@ -425,9 +473,14 @@ JobDesc edt_job(const iwpp_image *bin, int32_t *sq, int32_t *nn, int flags) {
 struct iwpp_plan {
     iwpp_ctx *ctx = nullptr;
     std::vector<iwpp_job> src;   // the jobs as given (re-prepared per option set)
-    std::vector<JobDesc> jobs;   // prepared descriptors (layout, TMA maps)
+    std::vector<JobDesc> jobs;   // all prepared descriptors
+    // launch groups (one, or one per operation family with batch_split):
+    // descriptors (layout, TMA maps), prepared launch, workspace offset
+    std::vector<std::vector<JobDesc>> gjobs;
+    std::vector<Prepared> parts;
+    std::vector<size_t> offs;
+    int fam = 0;                 // the family of the whole batch (tuning key)
     iwpp_options opt{};
-    Prepared P;
     void *ws = nullptr;
     size_t ws_bytes = 0;
     cudaStream_t cap = nullptr;  // private stream used for graph capture
@@ -465,26 +518,37 @@ int plan_prepare(iwpp_plan *p, const iwpp_options &opt) {
     p->jobs.clear();
     int rc = jobs_from(ctx, (int)p->src.size(), p->src.data(), p->jobs);
     if (rc) return rc;
-    rc = prepare(ctx, p->jobs, opt, p->P);
-    if (rc) return rc;
-    if (p->P.ws_bytes > p->ws_bytes) {
+    p->fam = pick_family(p->jobs);
+    p->gjobs = launch_groups(p->jobs, opt.batch_split);
+    p->parts.assign(p->gjobs.size(), Prepared());
+    p->offs.assign(p->gjobs.size(), 0);
+    size_t total = 0;
+    for (size_t k = 0; k < p->gjobs.size(); ++k) {
+        if ((rc = prepare(ctx, p->gjobs[k], opt, p->parts[k]))) return rc;
+        p->offs[k] = total;
+        total += align_up(p->parts[k].ws_bytes, 256);
+    }
+    if (total > p->ws_bytes) {
         if (p->ws) {
             CK(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
             cudaFree(p->ws);
             p->ws = nullptr;
             p->ws_bytes = 0;
         }
-        cudaError_t e = cudaMalloc(&p->ws, p->P.ws_bytes);
+        cudaError_t e = cudaMalloc(&p->ws, total);
         if (e != cudaSuccess) return fail(ctx, IWPP_ENOMEM, "plan workspace: %s", cudaGetErrorString(e));
-        p->ws_bytes = p->P.ws_bytes;
+        p->ws_bytes = total;
     }
-    bind_workspace(p->P, (char *)p->ws, ctx->ctl);
-    if (p->jobs.size() > 1)
-        CK(cudaMemcpy((char *)p->ws + p->P.o_jobs, p->jobs.data(), p->jobs.size() * sizeof(JobDesc),
-                      cudaMemcpyHostToDevice),
-           "job table upload");
+    for (size_t k = 0; k < p->gjobs.size(); ++k) {
+        char *ws = (char *)p->ws + p->offs[k];
+        bind_workspace(p->parts[k], ws, ctx->ctl);
+        if (p->gjobs[k].size() > 1)
+            CK(cudaMemcpy(ws + p->parts[k].o_jobs, p->gjobs[k].data(), p->gjobs[k].size() * sizeof(JobDesc),
+                          cudaMemcpyHostToDevice),
+               "job table upload");
+    }
     p->opt = opt;
-    p->key = plan_key(ctx, p->jobs, p->P.fam);
+    p->key = plan_key(ctx, p->jobs, p->fam);
     return IWPP_OK;
 }
 
@@ -515,6 +579,7 @@ int iwpp_ctx_create(iwpp_ctx **out, int device, size_t hbm_budget_bytes) {
     ctx->opt.edt_revisit_sweep_min = 64;
     ctx->opt.revisit_sweeps = -1;
     ctx->opt.gdt_sweeps = 8;
+    ctx->opt.batch_split = 1;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&ctx->ctl, sizeof(Control)) != cudaSuccess ||
@@ -558,7 +623,8 @@ int iwpp_set_options(iwpp_ctx *ctx, const iwpp_options *o) {
         o->timeout_ms < 1 || o->timeout_ms > 600000 || o->timing < 0 || o->timing > 1 ||
         o->revisit_sweep_min < 0 || o->edt_sweeps < 0 || o->edt_sweeps > 64 || o->edt_revisit_sweep_min < 0 ||
         o->revisit_sweeps < -1 || o->revisit_sweeps > 64 || o->queue_mode < 0 || o->queue_mode > 3 ||
-        o->test_empty_slot < 0 || o->test_empty_slot > 1 || o->gdt_sweeps < 0 || o->gdt_sweeps > 64)
+        o->test_empty_slot < 0 || o->test_empty_slot > 1 || o->gdt_sweeps < 0 || o->gdt_sweeps > 64 ||
+        o->batch_split < 0 || o->batch_split > 1)
         return fail(ctx, IWPP_EINVAL, "option out of range");
     ctx->opt = *o;
     return IWPP_OK;
@@ -819,11 +885,13 @@ int iwpp_plan_launch(iwpp_plan *p, void *stream) {
     if (!p) return IWPP_EINVAL;
     iwpp_ctx *ctx = p->ctx;
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-    int rc = enqueue(ctx, p->P, p->opt.max_relaunch, (cudaStream_t)stream, nullptr, nullptr);
-    if (rc) return rc;
-    ctx->launches += 3 + 3 * (uint64_t)p->opt.max_relaunch;
+    for (const Prepared &P : p->parts) {
+        int rc = enqueue(ctx, P, p->opt.max_relaunch, (cudaStream_t)stream, nullptr, nullptr);
+        if (rc) return rc;
+        ctx->launches += 3 + 3 * (uint64_t)p->opt.max_relaunch;
+        ctx->tiles_initial += (uint64_t)P.ntiles;
+    }
     ctx->calls += 1;
-    ctx->tiles_initial += (uint64_t)p->P.ntiles;
     return IWPP_OK;
 }
 
@@ -833,7 +901,9 @@ int iwpp_plan_launch_graph(iwpp_plan *p, void *stream) {
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     if (!p->exec) {
         CK(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-        const int rc = enqueue(ctx, p->P, p->opt.max_relaunch, p->cap, nullptr, nullptr);
+        int rc = IWPP_OK;
+        for (const Prepared &P : p->parts)
+            if (rc == IWPP_OK) rc = enqueue(ctx, P, p->opt.max_relaunch, p->cap, nullptr, nullptr);
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(p->cap, &g);
         if (rc) {
@@ -845,9 +915,11 @@ int iwpp_plan_launch_graph(iwpp_plan *p, void *stream) {
         CK(cudaGraphInstantiate(&p->exec, p->graph, 0), "cudaGraphInstantiate");
     }
     CK(cudaGraphLaunch(p->exec, (cudaStream_t)stream), "cudaGraphLaunch");
-    ctx->launches += 3 + 3 * (uint64_t)p->opt.max_relaunch;
+    for (const Prepared &P : p->parts) {
+        ctx->launches += 3 + 3 * (uint64_t)p->opt.max_relaunch;
+        ctx->tiles_initial += (uint64_t)P.ntiles;
+    }
     ctx->calls += 1;
-    ctx->tiles_initial += (uint64_t)p->P.ntiles;
     return IWPP_OK;
 }
 
@@ -863,19 +935,24 @@ int iwpp_plan_autotune(iwpp_plan *p, void *stream, int reps, iwpp_options *best)
     iwpp_options best_opt = base;
     float best_ms = 1e30f;
     int rc = IWPP_OK;
-    const int occ = ctx->occupancy[p->P.fam];
+    const int occ = ctx->occupancy[p->fam];
     // sweep candidates per operation; a mixed plan pairs them up
     const int sweeps_c[3] = {2, 3, 4};
     const int revisit_c[2] = {0, 32};
     const int edt_sweeps_c[3] = {1, 2, 3};
     const int edt_revisit_c[2] = {16, 64};
-    const int fam = p->P.fam;
+    const int fam = p->fam;
     const int bps_c[2] = {0, occ > 2 ? occ - 1 : 0};
+    // a batch of several operation families: one mixed launch, or one
+    // launch per family (then all CTAs per SM: occupancy differs per part)
+    const int nsplit = launch_groups(p->jobs, 1).size() > 1 ? 2 : 1;
+    for (int sp = 0; sp < nsplit && rc == IWPP_OK; ++sp)
     for (int a = 0; a < 3 && rc == IWPP_OK; ++a)
         for (int b = 0; b < 2 && rc == IWPP_OK; ++b)
             for (int c = 0; c < 2 && rc == IWPP_OK; ++c) {
-                if (c == 1 && bps_c[1] == 0) continue;
+                if (c == 1 && (bps_c[1] == 0 || sp == 1)) continue;
                 iwpp_options o = base;
+                o.batch_split = sp;
                 if (fam != FAM_EDT) {
                     o.sweeps = sweeps_c[a];
                     o.revisit_sweep_min = revisit_c[b];

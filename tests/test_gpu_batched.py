@@ -66,9 +66,29 @@ def test_run_jobs_mixed_batch(cuda_ctx):
     check(jobs, refs)
 
 
-def test_plan_launch_and_graph_replay(cuda_ctx):
+def test_run_jobs_split_by_family(cuda_ctx):
+    """batch_split: one persistent launch per operation family (uint8 and
+    int32 reconstruction, distance transform) back to back; same results."""
+    jobs, refs = make_jobs(16)
+    old = cuda_ctx.options()
+    cuda_ctx.set_options(batch_split=1)
+    try:
+        cuda_ctx.run_jobs(jobs)
+        torch.cuda.synchronize()
+    finally:
+        cuda_ctx.set_options(**old)
+    check(jobs, refs)
+
+
+@pytest.mark.parametrize("split", [0, 1])
+def test_plan_launch_and_graph_replay(cuda_ctx, split):
     jobs, refs = make_jobs(12)
-    plan = cuda_ctx.plan(jobs)
+    old = cuda_ctx.options()
+    cuda_ctx.set_options(batch_split=split)
+    try:
+        plan = cuda_ctx.plan(jobs)
+    finally:
+        cuda_ctx.set_options(**old)
     try:
         plan.launch()
         cuda_ctx.sync()
