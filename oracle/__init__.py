@@ -20,6 +20,14 @@ What it provides (paper = Teodoro et al., arXiv:1209.3314):
   {mask >= t} that meet {marker and mask >= t}.  Independent of Algorithm 2.
 * ``edt_bruteforce`` -- the definition of the distance map (Section 2.2):
   minimum squared distance to any feature pixel.
+* ``gdt`` / ``gdt_bellman_ford`` -- shortest paths on a grid with obstacles
+  (Section 1): Dijkstra's algorithm, and plain relaxation to a fixpoint.
+* ``watershed`` -- marker-controlled watershed by flooding (Section 1), the
+  image foresting transform with the highest-value path cost, sequential C;
+  ``watershed_levels_threshold`` / ``watershed_pdist_relax`` /
+  ``watershed_labels_reach`` restate its three parts independently
+  (threshold decomposition, relaxation to a fixpoint, per-label
+  reachability) for small images.
 * certificate checks of a result against the propagation rules.
 
 Every function takes and returns numpy arrays; the C part is built by
@@ -52,6 +60,7 @@ def _load():
                                           ctypes.c_uint64]
         lib.oracle_edt_exact.argtypes = [i32, i32, vp, i32, vp]
         lib.oracle_gdt.argtypes = [i32, i32, vp, vp, vp, i64p]
+        lib.oracle_watershed.argtypes = [i32, i32, vp, vp, vp, vp, vp, i64p]
         for f in ("oracle_fh_i32", "oracle_fh_u8", "oracle_edt",
                   "oracle_edt_policy", "oracle_edt_exact"):
             getattr(lib, f).restype = ctypes.c_int
@@ -168,6 +177,126 @@ def gdt_bellman_ford(mask: np.ndarray, seeds: np.ndarray) -> np.ndarray:
             break
         d = best
     return np.where(d >= INF, np.iinfo(np.int32).max, d).astype(np.int32)
+
+
+def watershed(relief: np.ndarray, markers: np.ndarray, stats: dict | None = None,
+              with_pdist: bool = False):
+    """Marker-controlled watershed by flooding (Section 1 names it as an
+    IWPP algorithm; the definition is in ``oracle_watershed`` in the C file):
+    returns (label int32, level in the relief's dtype[, plateau distance]).
+    Without markers the level is the dtype's maximum and the label 0."""
+    lib = _load()
+    f = np.asarray(relief)
+    assert f.dtype in (np.uint8, np.int32) and f.ndim == 2
+    m = np.ascontiguousarray(markers, dtype=np.int32)
+    assert m.shape == f.shape
+    h, w = f.shape
+    f32 = np.ascontiguousarray(f, dtype=np.int32)
+    label = np.empty((h, w), np.int32)
+    level = np.empty((h, w), np.int32)
+    pdist = np.empty((h, w), np.int32)
+    st = np.zeros(4, np.int64)
+    rc = lib.oracle_watershed(h, w, _ptr(f32), _ptr(m), _ptr(label), _ptr(level), _ptr(pdist),
+                              st.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if rc != 0:
+        raise MemoryError("oracle_watershed")
+    if stats is not None:
+        stats.update(pops=int(st[0]), improvements=int(st[1]), plateau_pushes=int(st[2]),
+                     label_pushes=int(st[3]))
+    if f.dtype == np.uint8:
+        level = np.minimum(level, 255).astype(np.uint8)
+    return (label, level, pdist) if with_pdist else (label, level)
+
+
+def _shifted(a: np.ndarray, dy: int, dx: int, fill) -> np.ndarray:
+    """out[y, x] = a[y + dy, x + dx], fill outside the image."""
+    h, w = a.shape
+    out = np.full_like(a, fill)
+    out[max(-dy, 0):h + min(-dy, 0), max(-dx, 0):w + min(-dx, 0)] = \
+        a[max(dy, 0):h + min(dy, 0), max(dx, 0):w + min(dx, 0)]
+    return out
+
+
+_OFF8 = [(dy, dx) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if dy or dx]
+
+
+def watershed_levels_threshold(relief: np.ndarray, markers: np.ndarray) -> np.ndarray:
+    """Flooding levels by threshold decomposition: level(p) is the least t
+    such that p lies in an 8-connected component of {relief <= t} that holds
+    a marker pixel (a path whose highest value is <= t exists exactly then).
+    int64; INT32_MAX where no marker exists."""
+    from scipy import ndimage
+
+    f = np.asarray(relief).astype(np.int64)
+    mk = np.asarray(markers) != 0
+    out = np.full(f.shape, np.iinfo(np.int32).max, np.int64)
+    if not mk.any():
+        return out
+    unset = np.ones(f.shape, bool)
+    for t in np.unique(f):
+        lab, n = ndimage.label(f <= t, structure=np.ones((3, 3), bool))
+        hit = np.zeros(n + 1, bool)
+        hit[lab[mk & (f <= t)]] = True
+        hit[0] = False
+        reached = hit[lab] & unset
+        out[reached] = t
+        unset &= ~reached
+    return out
+
+
+def watershed_pdist_relax(level: np.ndarray, markers: np.ndarray) -> np.ndarray:
+    """Plateau distances by relaxation to a fixpoint: 0 at marker pixels and
+    at pixels with a lower neighbour, else 1 + the least value over the
+    neighbours of equal level, repeated until nothing changes."""
+    lv = np.asarray(level).astype(np.int64)
+    TOP = np.iinfo(np.int64).max
+    INF = np.iinfo(np.int32).max
+    entry = np.asarray(markers) != 0
+    for dy, dx in _OFF8:
+        entry |= _shifted(lv, dy, dx, TOP) < lv
+    d = np.where(entry, 0, INF).astype(np.int64)
+    while True:
+        best = d.copy()
+        for dy, dx in _OFF8:
+            nd = _shifted(d, dy, dx, INF)
+            same = _shifted(lv, dy, dx, TOP) == lv
+            best = np.where(same & (nd < INF), np.minimum(best, nd + 1), best)
+        if np.array_equal(best, d):
+            return d
+        d = best
+
+
+def watershed_labels_reach(level: np.ndarray, pdist: np.ndarray, markers: np.ndarray) -> np.ndarray:
+    """Labels by reachability: for every marker value separately, the set of
+    pixels reachable from its marker pixels along optimal edges (p -> q, q
+    not a marker: level(p) < level(q) with pdist(q) = 0, or equal levels
+    with pdist(p) + 1 = pdist(q)) grown to a fixpoint; each pixel takes the
+    least value that reaches it, marker pixels keep theirs, 0 if none."""
+    lv = np.asarray(level).astype(np.int64)
+    pd = np.asarray(pdist).astype(np.int64)
+    mk = np.asarray(markers).astype(np.int64)
+    TOP = np.iinfo(np.int64).max
+    edges = []
+    for dy, dx in _OFF8:  # edge from the neighbour at (dy, dx) into p
+        nl = _shifted(lv, dy, dx, TOP)
+        npd = _shifted(pd, dy, dx, TOP)
+        rise = (nl < lv) & (pd == 0)
+        flat = (nl == lv) & (npd + 1 == pd)
+        edges.append((dy, dx, (rise | flat) & (mk == 0)))
+    out = mk.copy()
+    best = np.full(mk.shape, TOP, np.int64)
+    for L in np.unique(mk[mk != 0]):
+        r = mk == L
+        while True:
+            grow = r.copy()
+            for dy, dx, e in edges:
+                grow |= e & _shifted(r, dy, dx, False)
+            if np.array_equal(grow, r):
+                break
+            r = grow
+        best = np.where(r & (mk == 0), np.minimum(best, L), best)
+    out = np.where((mk == 0) & (best < TOP), best, out)
+    return out.astype(np.int32)
 
 
 def _neighbour_max(J: np.ndarray, conn: int) -> np.ndarray:

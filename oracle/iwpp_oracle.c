@@ -22,6 +22,12 @@
  *   oracle_gdt                    Shortest-path (geodesic) distance on a grid
  *                                 with obstacles, one of the IWPP uses named
  *                                 in Section 1, by Dijkstra's algorithm.
+ *   oracle_watershed              Marker-controlled watershed by flooding,
+ *                                 another IWPP use named in Section 1:
+ *                                 flooding levels by Dijkstra's algorithm on
+ *                                 the highest-value path cost, plateau
+ *                                 distances by breadth-first search, labels
+ *                                 by breadth-first search per marker label.
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *   - pixels outside the image do not exist (no padding, no wrap-around);
@@ -425,3 +431,167 @@ int oracle_gdt(int h, int w, const uint8_t *mask, const uint8_t *seed, int32_t *
     return 0;
 }
 
+
+/* ------------------------------------- watershed from markers (Section 1) */
+
+/*
+ * Marker-controlled watershed by flooding, named in Section 1 as an IWPP
+ * algorithm.  The paper defines none; the definition taken here is the
+ * image foresting transform with the highest-value path cost (Falcao,
+ * Stolfi and Lotufo, 2004) and the lexicographic plateau cost of Lotufo and
+ * Falcao (2000), with ties between basins settled by the least label:
+ *   f         relief, int32 (uint8 reliefs are widened by the caller);
+ *   markers   int32, 0 = no marker;
+ *   a path's cost is the highest relief value on it (both ends included);
+ *   level[p]  least cost of an 8-connected path from a marker pixel to p
+ *             (the flooding level; f[p] at a marker pixel);
+ *   pdist[p]  plateau distance: 0 at marker pixels and at pixels with a
+ *             neighbour of lower level (the entry of p's level region),
+ *             else 1 + the least pdist over neighbours of equal level;
+ *   optimal edge p -> q (q a neighbour of p, q not a marker):
+ *             level[p] < level[q] and pdist[q] = 0, or
+ *             level[p] = level[q] and pdist[p] + 1 = pdist[q];
+ *   label[q]  the least marker value among the marker pixels from which q
+ *             is reached along optimal edges (a marker pixel keeps its own).
+ * Optimal edges raise (level, pdist) strictly, so every label is settled by
+ * the labels below it and the result does not depend on any visiting order.
+ * Without markers nothing is reached: label 0, level and pdist INT32_MAX.
+ *
+ * Steps: (1) Dijkstra's algorithm on the highest-value cost from all marker
+ * pixels (binary heap, lazy deletion); (2) breadth-first search from every
+ * entry pixel at once across neighbours of equal level; (3) for each marker
+ * value in increasing order, a breadth-first search along optimal edges
+ * from its marker pixels that labels the pixels not labelled yet (a pixel
+ * reached earlier carries a smaller label, and what lies behind it is then
+ * reached with that smaller label as well).
+ * stats (optional): [0] heap pops, [1] level improvements, [2] plateau
+ * pushes, [3] label pushes.  Returns 0, or -1 on allocation failure.
+ */
+static int cmp_pair(const void *a, const void *b) {
+    const int64_t *x = (const int64_t *)a, *y = (const int64_t *)b;
+    if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;
+    return x[1] < y[1] ? -1 : (x[1] > y[1] ? 1 : 0);
+}
+
+int oracle_watershed(int h, int w, const int32_t *f, const int32_t *markers,
+                     int32_t *label, int32_t *level, int32_t *pdist,
+                     int64_t *stats) {
+    const int64_t n = (int64_t)h * w;
+    int64_t nm = 0;
+    for (int64_t i = 0; i < n; i++) nm += markers[i] != 0;
+    heap_item *hp = (heap_item *)malloc((size_t)(9 * n + 1) * sizeof(heap_item));
+    int64_t *lv = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *pairs = (int64_t *)malloc((size_t)(2 * nm + 2) * sizeof(int64_t));
+    uint8_t *done = (uint8_t *)calloc((size_t)n + 1, 1);
+    fifo_t q;
+    if (!hp || !lv || !pairs || !done || fifo_init(&q, n + 1) != 0) {
+        free(hp); free(lv); free(pairs); free(done);
+        return -1;
+    }
+    const int64_t INF = INT64_MAX;
+    int64_t hn = 0, pops = 0, improv = 0, ppush = 0, lpush = 0;
+
+    /* (1) flooding levels */
+    for (int64_t i = 0; i < n; i++) {
+        lv[i] = INF;
+        if (markers[i]) {
+            lv[i] = f[i];
+            heap_push(hp, &hn, lv[i], i);
+        }
+    }
+    while (hn > 0) {
+        heap_item it = heap_pop(hp, &hn);
+        pops++;
+        if (it.key > lv[it.idx]) continue; /* stale entry */
+        const int y = (int)(it.idx / w), x = (int)(it.idx % w);
+        for (int k = 0; k < 8; k++) {
+            const int qy = y + NB8[k][0], qx = x + NB8[k][1];
+            if (!inside(qy, qx, h, w)) continue;
+            const int64_t qq = (int64_t)qy * w + qx;
+            const int64_t c = it.key > f[qq] ? it.key : f[qq];
+            if (c < lv[qq]) {
+                lv[qq] = c;
+                heap_push(hp, &hn, c, qq);
+                improv++;
+            }
+        }
+    }
+
+    /* (2) plateau distances: entry pixels first, then breadth-first across
+     * equal levels */
+    for (int64_t i = 0; i < n; i++) {
+        pdist[i] = INT32_MAX;
+        if (lv[i] == INF) continue;
+        int entry = markers[i] != 0;
+        const int y = (int)(i / w), x = (int)(i % w);
+        for (int k = 0; k < 8 && !entry; k++) {
+            const int qy = y + NB8[k][0], qx = x + NB8[k][1];
+            if (inside(qy, qx, h, w) && lv[(int64_t)qy * w + qx] < lv[i]) entry = 1;
+        }
+        if (entry) {
+            pdist[i] = 0;
+            fifo_push(&q, i);
+            ppush++;
+        }
+    }
+    while (q.head < q.tail) {
+        const int64_t p = fifo_pop(&q, 0, NULL);
+        const int y = (int)(p / w), x = (int)(p % w);
+        for (int k = 0; k < 8; k++) {
+            const int qy = y + NB8[k][0], qx = x + NB8[k][1];
+            if (!inside(qy, qx, h, w)) continue;
+            const int64_t qq = (int64_t)qy * w + qx;
+            if (lv[qq] == lv[p] && pdist[qq] == INT32_MAX) {
+                pdist[qq] = pdist[p] + 1;
+                fifo_push(&q, qq);
+                ppush++;
+            }
+        }
+    }
+
+    /* (3) labels, one marker value at a time in increasing order */
+    int64_t np = 0;
+    for (int64_t i = 0; i < n; i++) {
+        label[i] = markers[i];
+        if (markers[i]) {
+            pairs[2 * np] = markers[i];
+            pairs[2 * np + 1] = i;
+            np++;
+            done[i] = 1;
+        }
+    }
+    qsort(pairs, (size_t)np, 2 * sizeof(int64_t), cmp_pair);
+    for (int64_t a = 0; a < np;) {
+        int64_t b = a;
+        q.head = q.tail = 0;
+        while (b < np && pairs[2 * b] == pairs[2 * a]) {
+            fifo_push(&q, pairs[2 * b + 1]);
+            b++;
+        }
+        const int32_t L = (int32_t)pairs[2 * a];
+        while (q.head < q.tail) {
+            const int64_t p = fifo_pop(&q, 0, NULL);
+            const int y = (int)(p / w), x = (int)(p % w);
+            for (int k = 0; k < 8; k++) {
+                const int qy = y + NB8[k][0], qx = x + NB8[k][1];
+                if (!inside(qy, qx, h, w)) continue;
+                const int64_t qq = (int64_t)qy * w + qx;
+                if (done[qq]) continue; /* a marker, or labelled by a smaller value */
+                const int rise = lv[p] < lv[qq] && pdist[qq] == 0;
+                const int flat = lv[p] == lv[qq] && (int64_t)pdist[p] + 1 == pdist[qq];
+                if (rise || flat) {
+                    label[qq] = L;
+                    done[qq] = 1;
+                    fifo_push(&q, qq);
+                    lpush++;
+                }
+            }
+        }
+        a = b;
+    }
+    for (int64_t i = 0; i < n; i++) level[i] = lv[i] == INF ? INT32_MAX : (int32_t)lv[i];
+    fifo_free(&q);
+    free(hp); free(lv); free(pairs); free(done);
+    if (stats) { stats[0] = pops; stats[1] = improv; stats[2] = ppush; stats[3] = lpush; }
+    return 0;
+}

@@ -32,6 +32,16 @@ MUTATIONS = {
     # exact EDT (Meijster)
     "exact_column_scan_off_by_one": ("if (below < g[(int64_t)y * w + x]) g[(int64_t)y * w + x] = 1 + below;",
                                      "if (below < g[(int64_t)y * w + x]) g[(int64_t)y * w + x] = below;"),
+    # watershed (Section 1): levels, plateau distances, labels
+    "ws_level_ignores_relief": ("const int64_t c = it.key > f[qq] ? it.key : f[qq];",
+                                "const int64_t c = it.key;"),
+    "ws_entry_from_higher": ("lv[(int64_t)qy * w + qx] < lv[i]) entry = 1;",
+                             "lv[(int64_t)qy * w + qx] > lv[i]) entry = 1;"),
+    "ws_rise_from_equal_level": ("const int rise = lv[p] < lv[qq] && pdist[qq] == 0;",
+                                 "const int rise = lv[p] <= lv[qq] && pdist[qq] == 0;"),
+    "ws_flat_sideways": ("(int64_t)pdist[p] + 1 == pdist[qq];", "(int64_t)pdist[p] <= pdist[qq];"),
+    "ws_largest_label_first": ("if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;",
+                               "if (x[0] != y[0]) return x[0] < y[0] ? 1 : -1;"),
     "exact_separator_sign": ("int64_t num = (int64_t)u * u - i * i + gy[u] * gy[u] - gy[i] * gy[i];",
                              "int64_t num = (int64_t)u * u - i * i - gy[u] * gy[u] + gy[i] * gy[i];"),
 }
@@ -106,11 +116,33 @@ def _exact_pins_fail(lib):
     return False
 
 
+def _ws_pins_fail(lib):
+    rng = np.random.default_rng(80)
+    for it in range(150):
+        h, w = (int(v) for v in rng.integers(1, 16, 2))
+        f = rng.integers(0, (2, 4, 256)[it % 3], (h, w)).astype(np.int32)
+        m = np.zeros((h, w), np.int32)
+        for _ in range(int(rng.integers(1, 6))):
+            m[rng.integers(0, h), rng.integers(0, w)] = rng.integers(1, 6)
+        label, level, pdist = (np.empty((h, w), np.int32) for _ in range(3))
+        vp = ctypes.c_void_p
+        lib.oracle_watershed(ctypes.c_int(h), ctypes.c_int(w), f.ctypes.data_as(vp), m.ctypes.data_as(vp),
+                             label.ctypes.data_as(vp), level.ctypes.data_as(vp), pdist.ctypes.data_as(vp), None)
+        t = oracle.watershed_levels_threshold(f, m)
+        pr = oracle.watershed_pdist_relax(t, m)
+        if (not np.array_equal(level, t) or not np.array_equal(pdist, pr)
+                or not np.array_equal(label, oracle.watershed_labels_reach(t, pr, m))):
+            return True
+    return False
+
+
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_is_caught(tmp_path, name):
     lib = _mutant(tmp_path, name)
     if name.startswith("edt_"):
         assert _edt_pins_fail(lib), f"mutation {name} not detected"
+    elif name.startswith("ws_"):
+        assert _ws_pins_fail(lib), f"mutation {name} not detected"
     elif name.startswith("exact_"):
         assert _exact_pins_fail(lib), f"mutation {name} not detected"
     else:
