@@ -86,7 +86,7 @@ typedef struct {
  * sweeps 3, queue_factor 32, spill_cap 8192, max_relaunch 1, timeout_ms
  * 10000, timing 0, revisit_sweep_min 0, edt_sweeps 2, edt_revisit_sweep_min
  * 64, revisit_sweeps -1, queue_mode 0, test_empty_slot 0, gdt_sweeps 8,
- * batch_split 1.  tile = 0 lets the autotuner choose.  Values are validated
+ * batch_split 1, ws_sweeps 4.  tile = 0 lets the autotuner choose.  Values are validated
  * by iwpp_set_options().  New fields are only ever appended. */
 typedef struct {
     int32_t tile;            /* tile side in pixels: 0 (auto) or 64           */
@@ -130,6 +130,8 @@ typedef struct {
                                 operation family, back to back on the stream
                                 (each with its smaller, faster kernel; the
                                 default); the autotuner tries both            */
+    int32_t ws_sweeps;       /* watershed plateau-distance and label
+                                propagations: sweep sets per bulk visit       */
 } iwpp_options;
 
 /* Creates a context on `device`.  hbm_budget_bytes bounds the workspace the
@@ -208,6 +210,37 @@ int iwpp_geodesic(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image *seeds
                   int32_t *dist, void *stream);
 int iwpp_geodesic_async(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image *seeds,
                         int32_t *dist, void *stream);
+
+/*
+ * Watershed from markers, which Section 1 names among the IWPP algorithms,
+ * as three wavefront propagations on the tile wavefront.  The paper gives
+ * no definition; this is the image foresting transform with the
+ * highest-value path cost (Falcao, Stolfi and Lotufo, 2004), plateaus
+ * split by distance (Lotufo and Falcao, 2000), ties to the least label:
+ *   relief   IWPP_U8 or IWPP_I32 image; markers: IWPP_I32 image of the
+ *            same shape (pitches may differ), 0 = no marker, any other
+ *            value but INT32_MAX a label;
+ *   levels   (optional, may be NULL: dense h*w of the relief's type,
+ *            device) the flooding level: the least, over the 8-connected
+ *            paths from a marker pixel, of the highest relief value on the
+ *            path (a marker pixel's own relief value);
+ *   labels   (dense h*w int32, device) the least marker value among the
+ *            marker pixels from which the pixel is reached along optimal
+ *            edges: from a lower-level neighbour into a pixel with one, or
+ *            within a level region from a neighbour one breadth-first step
+ *            nearer to the region's entry pixels (its markers and its
+ *            pixels with a lower neighbour).  A marker pixel keeps its
+ *            value.  Without any marker: labels 0 and levels the type's
+ *            maximum.
+ * The result is unique (no dependence on the processing order).  Steps:
+ * the levels by a reconstruction by dilation of the complemented images,
+ * then the plateau distances and the labels by min-propagations along
+ * per-pixel in-edge masks.  labels and levels must not overlap the inputs.
+ * The context holds 2*h*w*size(relief) + 5*h*w bytes of planes besides
+ * its workspace.  Limits: h*w <= 2^30.  Synchronous.
+ */
+int iwpp_watershed(iwpp_ctx *ctx, const iwpp_image *relief, const iwpp_image *markers,
+                   int32_t *labels, void *levels, void *stream);
 
 /*
  * Batched entry points: n independent images in ONE persistent launch

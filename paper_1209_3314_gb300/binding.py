@@ -51,7 +51,8 @@ class Options(ctypes.Structure):
                 ("revisit_sweep_min", ctypes.c_int32), ("edt_sweeps", ctypes.c_int32),
                 ("edt_revisit_sweep_min", ctypes.c_int32), ("revisit_sweeps", ctypes.c_int32),
                 ("queue_mode", ctypes.c_int32), ("test_empty_slot", ctypes.c_int32),
-                ("gdt_sweeps", ctypes.c_int32), ("batch_split", ctypes.c_int32)]
+                ("gdt_sweeps", ctypes.c_int32), ("batch_split", ctypes.c_int32),
+                ("ws_sweeps", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -88,6 +89,7 @@ SIGNATURES = {
     "iwpp_edt_exact": (_i32, [_vp, ctypes.POINTER(Image), _vp, _vp, _i32, _vp]),
     "iwpp_geodesic": (_i32, [_vp, ctypes.POINTER(Image), ctypes.POINTER(Image), _vp, _vp]),
     "iwpp_geodesic_async": (_i32, [_vp, ctypes.POINTER(Image), ctypes.POINTER(Image), _vp, _vp]),
+    "iwpp_watershed": (_i32, [_vp, ctypes.POINTER(Image), ctypes.POINTER(Image), _vp, _vp, _vp]),
     "iwpp_recon_batched": (_i32, [_vp, _i32, ctypes.POINTER(Image), ctypes.POINTER(Image), _i32,
                                   ctypes.POINTER(Image), _vp]),
     "iwpp_edt_batched": (_i32, [_vp, _i32, ctypes.POINTER(Image), ctypes.POINTER(_vp),
@@ -295,6 +297,30 @@ class Context:
         self._check(fn(self.h, ctypes.byref(m), ctypes.byref(s), ctypes.c_void_p(dist.data_ptr()),
                        _stream_ptr(stream)))
         return dist
+
+    def watershed(self, relief, markers, labels=None, levels=None, with_levels: bool = False,
+                  stream=None):
+        """Watershed from markers: relief (uint8 or int32 CUDA tensor),
+        markers (int32 CUDA tensor of the same shape, 0 = no marker).
+        Returns labels (int32), or (labels, levels) with with_levels (levels
+        in the relief's dtype: the flooding level of each pixel)."""
+        torch = _torch()
+        h, w = relief.shape
+        if labels is None:
+            labels = torch.empty((h, w), dtype=torch.int32, device=relief.device)
+        if with_levels and levels is None:
+            levels = torch.empty((h, w), dtype=relief.dtype, device=relief.device)
+        if labels.dtype != torch.int32 or tuple(labels.shape) != (h, w) or not labels.is_contiguous() \
+                or not labels.is_cuda:
+            raise ValueError("labels must be a contiguous int32 CUDA tensor of the image shape")
+        if levels is not None and (levels.dtype != relief.dtype or tuple(levels.shape) != (h, w)
+                                   or not levels.is_contiguous() or not levels.is_cuda):
+            raise ValueError("levels must be a contiguous CUDA tensor of the relief's dtype and shape")
+        f, m = image_of(relief), image_of(markers)
+        lv = ctypes.c_void_p(levels.data_ptr()) if levels is not None else None
+        self._check(self.lib.iwpp_watershed(self.h, ctypes.byref(f), ctypes.byref(m),
+                                            ctypes.c_void_p(labels.data_ptr()), lv, _stream_ptr(stream)))
+        return (labels, levels) if levels is not None else labels
 
     def recon_batched(self, markers, masks, conn: int = 8, outs=None, stream=None):
         torch = _torch()

@@ -15,7 +15,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libiwpp.so")
 
-SOURCES = ["iwpp_kernels.cu", "iwpp_api.cu", "iwpp_noalloc.cu", "iwpp_server.cu", "iwpp_edt_exact.cu"]
+SOURCES = ["iwpp_kernels.cu", "iwpp_api.cu", "iwpp_noalloc.cu", "iwpp_server.cu", "iwpp_edt_exact.cu",
+           "iwpp_watershed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -22,6 +22,8 @@ struct iwpp_ctx {
     char err[256] = {0};
     void *ws = nullptr;        // workspace arena
     size_t ws_bytes = 0;
+    void *aux = nullptr;       // planes of multi-step operations (watershed)
+    size_t aux_bytes = 0;
     Control *ctl = nullptr;    // device control block (own allocation, persistent counters)
     Control *h_ctl = nullptr;  // pinned host copy
     uint64_t calls = 0;
@@ -79,6 +81,7 @@ bool overlaps(const iwpp_image *a, const iwpp_image *b) {
 int pick_family(const std::vector<JobDesc> &jobs) {
     bool r8 = false, r32 = false, e = false;
     if (!jobs.empty() && jobs[0].op == OP_GDT) return FAM_GDT;  // geodesic launches hold only geodesic jobs
+    if (!jobs.empty() && (jobs[0].op == OP_WS_DIST || jobs[0].op == OP_WS_LABEL)) return FAM_WS;
     for (const JobDesc &j : jobs) {
         if (j.op == OP_EDT) e = true;
         else if (j.dtype == DT_U8) r8 = true;
@@ -134,6 +137,11 @@ void make_maps(JobDesc &d) {
     if (d.op == OP_GDT) {  // mask, sources, current result
         d.use_tma = make_map(&d.tm[0], d.a, DT_U8, d.h, d.w, d.pa) &&
                     make_map(&d.tm[1], d.b, DT_U8, d.h, d.w, d.pb) &&
+                    make_map(&d.tm[2], d.out, DT_I32, d.h, d.w, d.po);
+        return;
+    }
+    if (d.op == OP_WS_DIST || d.op == OP_WS_LABEL) {  // in-edge masks, values
+        d.use_tma = make_map(&d.tm[0], d.a, DT_U8, d.h, d.w, d.pa) &&
                     make_map(&d.tm[2], d.out, DT_I32, d.h, d.w, d.po);
         return;
     }
@@ -249,6 +257,7 @@ int prepare(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, const iwpp_options &opt, 
     ka.queue_mode = opt.queue_mode;
     ka.test_empty_slot = opt.test_empty_slot;
     ka.gdt_sweeps = opt.gdt_sweeps;
+    ka.ws_sweeps = opt.ws_sweeps;
     ka.timeout_ns = (unsigned long long)opt.timeout_ms * 1000000ull;
     return IWPP_OK;
 }
@@ -286,16 +295,18 @@ int enqueue(iwpp_ctx *ctx, const Prepared &P, int max_relaunch, cudaStream_t st,
 
 // The launch groups of a batch: all jobs together, or (batch_split) one
 // group per operation family -- uint8 reconstruction, int32
-// reconstruction, distance transform, shortest paths -- in that order.
+// reconstruction, distance transform, shortest paths, watershed steps --
+// in that order.
 std::vector<std::vector<JobDesc>> launch_groups(const std::vector<JobDesc> &jobs, int split) {
     std::vector<std::vector<JobDesc>> g;
     if (!split) {
         g.push_back(jobs);
         return g;
     }
-    std::vector<JobDesc> by[4];
+    std::vector<JobDesc> by[5];
     for (const JobDesc &j : jobs) {
-        const int k = j.op == OP_RECON ? (j.dtype == DT_U8 ? 0 : 1) : (j.op == OP_EDT ? 2 : 3);
+        const int k = j.op == OP_RECON ? (j.dtype == DT_U8 ? 0 : 1)
+                                       : (j.op == OP_EDT ? 2 : (j.op == OP_GDT ? 3 : 4));
         by[k].push_back(j);
     }
     for (auto &v : by)
@@ -442,6 +453,63 @@ JobDesc gdt_job(const iwpp_image *mask, const iwpp_image *seeds, int32_t *dist) 
     return d;
 }
 
+int ensure_aux(iwpp_ctx *ctx, size_t bytes, cudaStream_t st) {
+    if (bytes <= ctx->aux_bytes) return IWPP_OK;
+    if (ctx->budget && bytes > ctx->budget)
+        return fail(ctx, IWPP_ENOMEM, "planes of %zu bytes exceed the context budget of %zu", bytes, ctx->budget);
+    if (ctx->aux) {
+        CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+        CK(cudaFree(ctx->aux), "cudaFree");
+        ctx->aux = nullptr;
+        ctx->aux_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&ctx->aux, bytes);
+    if (e != cudaSuccess) {
+        ctx->aux = nullptr;
+        return fail(ctx, IWPP_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->aux_bytes = bytes;
+    return IWPP_OK;
+}
+
+int check_ws(iwpp_ctx *ctx, const iwpp_image *relief, const iwpp_image *markers, const int32_t *labels,
+             const void *levels) {
+    int rc;
+    if ((rc = check_image(ctx, relief, "relief")) || (rc = check_image(ctx, markers, "markers"))) return rc;
+    if (markers->dtype != IWPP_I32) return fail(ctx, IWPP_EINVAL, "watershed: markers must be int32");
+    if (relief->h != markers->h || relief->w != markers->w)
+        return fail(ctx, IWPP_EINVAL, "watershed: relief and markers must have the same shape");
+    if (!labels) return fail(ctx, IWPP_EINVAL, "null output pointer");
+    if ((int64_t)relief->h * relief->w > ((int64_t)1 << 30))
+        return fail(ctx, IWPP_EINVAL, "watershed limited to h*w <= 2^30");
+    iwpp_image lab{const_cast<int32_t *>(labels), relief->h, relief->w, relief->w, IWPP_I32};
+    if (overlaps(&lab, relief) || overlaps(&lab, markers))
+        return fail(ctx, IWPP_EINVAL, "labels must not alias the relief or the markers");
+    if (levels) {
+        iwpp_image lv{const_cast<void *>(levels), relief->h, relief->w, relief->w, relief->dtype};
+        if (overlaps(&lv, relief) || overlaps(&lv, markers) || overlaps(&lv, &lab))
+            return fail(ctx, IWPP_EINVAL, "levels must not alias the relief, the markers or the labels");
+    }
+    return IWPP_OK;
+}
+
+// A propagation step of the watershed: in-edge masks E, values V (both
+// dense planes).
+JobDesc ws_job(int op, int h, int w, const uint8_t *E, int32_t *V) {
+    JobDesc d;
+    memset(&d, 0, sizeof d);
+    d.op = op;
+    d.dtype = DT_U8;
+    d.conn = 8;
+    d.h = h;
+    d.w = w;
+    d.a = E;
+    d.out = V;
+    d.pa = w;
+    d.po = w;
+    return d;
+}
+
 JobDesc edt_job(const iwpp_image *bin, int32_t *sq, int32_t *nn, int flags) {
     JobDesc d;
     memset(&d, 0, sizeof d);
@@ -580,6 +648,7 @@ int iwpp_ctx_create(iwpp_ctx **out, int device, size_t hbm_budget_bytes) {
     ctx->opt.revisit_sweeps = -1;
     ctx->opt.gdt_sweeps = 8;
     ctx->opt.batch_split = 1;
+    ctx->opt.ws_sweeps = 4;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&ctx->ctl, sizeof(Control)) != cudaSuccess ||
@@ -599,6 +668,7 @@ int iwpp_ctx_destroy(iwpp_ctx *ctx) {
     if (!ctx) return IWPP_OK;
     cudaSetDevice(ctx->device);
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->aux) cudaFree(ctx->aux);
     if (ctx->ctl) cudaFree(ctx->ctl);
     for (auto &ev : ctx->pending_events) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
     for (auto &ev : ctx->free_events) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
@@ -624,7 +694,7 @@ int iwpp_set_options(iwpp_ctx *ctx, const iwpp_options *o) {
         o->revisit_sweep_min < 0 || o->edt_sweeps < 0 || o->edt_sweeps > 64 || o->edt_revisit_sweep_min < 0 ||
         o->revisit_sweeps < -1 || o->revisit_sweeps > 64 || o->queue_mode < 0 || o->queue_mode > 3 ||
         o->test_empty_slot < 0 || o->test_empty_slot > 1 || o->gdt_sweeps < 0 || o->gdt_sweeps > 64 ||
-        o->batch_split < 0 || o->batch_split > 1)
+        o->batch_split < 0 || o->batch_split > 1 || o->ws_sweeps < 0 || o->ws_sweeps > 64)
         return fail(ctx, IWPP_EINVAL, "option out of range");
     ctx->opt = *o;
     return IWPP_OK;
@@ -680,6 +750,51 @@ int iwpp_geodesic_async(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image 
     if (rc) return rc;
     std::vector<JobDesc> jobs{gdt_job(mask, seeds, dist)};
     return run(ctx, jobs, (cudaStream_t)stream, false);
+}
+
+int iwpp_watershed(iwpp_ctx *ctx, const iwpp_image *relief, const iwpp_image *markers, int32_t *labels,
+                   void *levels, void *stream) {
+    if (!ctx) return IWPP_EINVAL;
+    int rc = check_ws(ctx, relief, markers, labels, levels);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int h = relief->h, w = relief->w;
+    const int dt = relief->dtype == IWPP_U8 ? DT_U8 : DT_I32;
+    const size_t n = (size_t)h * w, es = dt == DT_U8 ? 1 : 4;
+    const size_t oA = 0, oB = align_up(n * es, 256), oE = oB + align_up(n * es, 256), oD = oE + align_up(n, 256);
+    if ((rc = ensure_aux(ctx, oD + align_up(n * 4, 256), st))) return rc;
+    char *aux = (char *)ctx->aux;
+    WsArgs a;
+    a.relief = relief->data;
+    a.markers = (const int32_t *)markers->data;
+    a.pf = relief->pitch;
+    a.pm = markers->pitch;
+    a.h = h;
+    a.w = w;
+    a.dtype = dt;
+    a.A = aux + oA;
+    a.B = aux + oB;
+    a.E = (uint8_t *)(aux + oE);
+    a.D = (int32_t *)(aux + oD);
+    a.labels = labels;
+    a.levels = levels;
+    // 1. flooding levels: reconstruction by dilation of the complements
+    CK(launch_ws_complement(a, st), "watershed complement launch");
+    iwpp_image A{a.A, h, w, w, relief->dtype}, B{a.B, h, w, w, relief->dtype};
+    std::vector<JobDesc> j1{recon_job(&A, &B, 8, &A)};
+    if ((rc = run(ctx, j1, st, false))) return rc;
+    // 2. plateau distances
+    CK(launch_ws_plateau_init(a, st), "watershed plateau init launch");
+    std::vector<JobDesc> j2{ws_job(OP_WS_DIST, h, w, a.E, a.D)};
+    if ((rc = run(ctx, j2, st, false))) return rc;
+    // 3. labels
+    CK(launch_ws_label_init(a, st), "watershed label init launch");
+    std::vector<JobDesc> j3{ws_job(OP_WS_LABEL, h, w, a.E, labels)};
+    if ((rc = run(ctx, j3, st, false))) return rc;
+    ctx->launches += 3;
+    ctx->calls -= 2;  // the three propagations are one call
+    return iwpp_sync(ctx, st);
 }
 
 int iwpp_edt_exact(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist, int32_t *nearest, int flags,

@@ -10,13 +10,25 @@
 
 namespace iwpp {
 
-enum : int { OP_RECON = 0, OP_EDT = 1, OP_GDT = 2 };
+// OP_WS_DIST / OP_WS_LABEL: the plateau-distance and label propagations of
+// the watershed from markers (min-propagations along per-pixel in-edge masks)
+enum : int { OP_RECON = 0, OP_EDT = 1, OP_GDT = 2, OP_WS_DIST = 3, OP_WS_LABEL = 4 };
 enum : int { DT_U8 = 0, DT_I32 = 1 };
 
 // kernel families (one persistent-kernel instantiation each)
-enum : int { FAM_RECON_U8 = 0, FAM_RECON_I32 = 1, FAM_EDT = 2, FAM_MIXED = 3, FAM_GDT = 4, FAM_COUNT = 5 };
+enum : int { FAM_RECON_U8 = 0, FAM_RECON_I32 = 1, FAM_EDT = 2, FAM_MIXED = 3, FAM_GDT = 4, FAM_WS = 5, FAM_COUNT = 6 };
 
 constexpr int TILE = 64;  // tile side in pixels
+
+// The 8-neighbour order of the kernels: neighbour k of p is p + (nb8_dy(k),
+// nb8_dx(k)) = (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1); 7 - k
+// is the mirror of k.  Bit k of a watershed in-edge mask says that
+// neighbour k may lower the pixel.
+__host__ __device__ constexpr int nb8_dy(int k) { return k < 3 ? -1 : (k < 5 ? 0 : 1); }
+__host__ __device__ constexpr int nb8_dx(int k) {
+    return (k == 0 || k == 3 || k == 5) ? -1 : ((k == 2 || k == 4 || k == 7) ? 1 : 0);
+}
+constexpr int WS_DINF = 0x3FFFFFFF;  // plateau distance of a pixel not reached (yet)
 
 // One image job inside a launch.  Tiles of job j have global ids
 // [tile_base, tile_base + tiles_x * tiles_y).
@@ -56,6 +68,7 @@ struct alignas(64) KArgs {
     int queue_mode;       // queue ablation: bit 0 per-thread atomics, bit 1 global-only
     int test_empty_slot;  // timeout-path tests: initial queue slot 0 left unfilled
     int gdt_sweeps;       // shortest paths: sweep sets per bulk visit
+    int ws_sweeps;        // watershed propagations: sweep sets per bulk visit
     unsigned long long timeout_ns;
 };
 
@@ -72,6 +85,23 @@ struct ExactArgs {
 };
 int exact_bands(int h);
 cudaError_t launch_edt_exact(const ExactArgs &a, cudaStream_t s);
+
+// Watershed from markers, per-pixel steps (iwpp_watershed.cu).  Planes are
+// dense (pitch w): A and B of the relief's type, E uint8, D and labels int32.
+struct WsArgs {
+    const void *relief;   // u8 or i32, pitch `pf` elements
+    const int32_t *markers;
+    int64_t pf, pm;       // pitches in elements
+    int h, w, dtype;      // DT_U8 / DT_I32
+    void *A, *B;          // complemented marker / mask; A holds the complemented levels after the reconstruction
+    uint8_t *E;           // in-edge masks
+    int32_t *D;           // plateau distances
+    int32_t *labels;
+    void *levels;         // optional flooding-level output (relief's type)
+};
+cudaError_t launch_ws_complement(const WsArgs &a, cudaStream_t s);
+cudaError_t launch_ws_plateau_init(const WsArgs &a, cudaStream_t s);
+cudaError_t launch_ws_label_init(const WsArgs &a, cudaStream_t s);
 
 // Launch helpers implemented in iwpp_kernels.cu.
 int family_threads(int fam);

@@ -98,12 +98,14 @@ constexpr int G_D = HDR_BYTES, G_M = G_D + BI32_PAD, G_U = 25984;
 constexpr int G_BYTES = G_U + BU8_BYTES;
 static_assert(G_M + BU8_BYTES <= G_U && G_U % 128 == 0 && G_M % 128 == 0 && 2 * QCAP_G * 2 <= BU8_BYTES,
               "geodesic layout");
+// watershed propagations: the same V / E boxes, the block queues after them
+constexpr int WS_BYTES = G_U + 2 * QCAP_G * 2;
 constexpr int FAM_SMEM[FAM_COUNT] = {RU8_BYTES, RI32_BYTES, E_BYTES,
-                                     cmax(cmax(RU8_BYTES, RI32_BYTES), E_BYTES), G_BYTES};
-constexpr int FAM_NT[FAM_COUNT] = {64, 64, 128, 128, 64};
+                                     cmax(cmax(RU8_BYTES, RI32_BYTES), E_BYTES), G_BYTES, WS_BYTES};
+constexpr int FAM_NT[FAM_COUNT] = {64, 64, 128, 128, 64, 64};
 // resident CTAs per SM that each family's shared memory allows; the
 // register budget is sized for them
-constexpr int FAM_MINB[FAM_COUNT] = {14, 5, 8, 5, 7};
+constexpr int FAM_MINB[FAM_COUNT] = {14, 5, 8, 5, 7, 7};
 
 // neighbourhood offsets (dy, dx); 8-connected: the first 4 are N+ (raster)
 __device__ __forceinline__ int nb_dy(int conn, int k) {
@@ -1640,6 +1642,294 @@ __device__ bool gdt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
 }
 
 // =====================================================================
+// Watershed from markers (Section 1's further IWPP use): plateau
+// distances and labels
+// =====================================================================
+//
+// Two min-propagations along fixed directed edges, given per pixel as an
+// in-edge mask E (bit k: neighbour k may lower the pixel) that the
+// per-pixel kernels of iwpp_watershed.cu build from the flooding levels:
+//   plateau distance (PLAT): V(q) = min(V(q), V(p) + 1) over edges between
+//     neighbours of equal level; entry pixels start at 0, the rest at
+//     WS_DINF;
+//   labels: V(q) = min(V(q), V(p)) over the optimal edges; marker pixels
+//     have no in-edges and keep their value; 0 (no label) is held as
+//     INT_MAX while the tile is staged.
+// Wavefront element: a pixel whose value can lower an out-neighbour.  The
+// sweeps, seeding, queue rounds and border test follow the shortest-path
+// family with the edge mask in place of the obstacle mask.
+
+template <bool PLAT>
+constexpr int WS_INF = PLAT ? WS_DINF : INT_MAX;
+
+template <bool PLAT>
+__device__ __forceinline__ int ws_cand(int v) { return PLAT ? v + 1 : v; }
+
+template <int DIR, bool PLAT>
+__device__ __forceinline__ bool ws_row_pass(int *__restrict__ V, const uint8_t *__restrict__ E, int r) {
+    constexpr unsigned FROM = DIR > 0 ? 1u << 3 : 1u << 4;  // the left / right neighbour
+    const int base = gcell(r, 0), eb = gmask(r, 0);
+    int run = V[base + (DIR > 0 ? 0 : TS + 1)];
+    bool ch = false;
+#pragma unroll 4
+    for (int s = 1; s <= TS; ++s) {
+        const int c = DIR > 0 ? s : TS + 1 - s;
+        const int o = V[base + c];
+        const int v = (E[eb + c] & FROM) ? min(o, ws_cand<PLAT>(run)) : o;
+        if (v != o) { V[base + c] = v; ch = true; }
+        run = v;
+    }
+    return ch;
+}
+
+// column pass; the diagonal neighbours of the previous row are read from
+// shared memory (old or new: both are values the pixel held)
+template <int DIR, bool PLAT>
+__device__ __forceinline__ bool ws_column_pass(int *__restrict__ V, const uint8_t *__restrict__ E, int t) {
+    // in-edge bits of the previous row's straight, left and right neighbours
+    constexpr unsigned BS = DIR > 0 ? 1u << 1 : 1u << 6;
+    constexpr unsigned BL = DIR > 0 ? 1u << 0 : 1u << 5;
+    constexpr unsigned BR = DIR > 0 ? 1u << 2 : 1u << 7;
+    const int c = t + 1;
+    int up = V[gcell(DIR > 0 ? 0 : RR - 1, c)];
+    bool ch = false;
+#pragma unroll 4
+    for (int s = 1; s <= TS; ++s) {
+        const int r = DIR > 0 ? s : RR - 1 - s;
+        const int i = gcell(r, c), ip = i - DIR * BI32_W;
+        const unsigned e = E[gmask(r, c)];
+        const int o = V[i];
+        int v = o;
+        if (e & BS) v = min(v, ws_cand<PLAT>(up));
+        if (e & BL) v = min(v, ws_cand<PLAT>(V[ip - 1]));
+        if (e & BR) v = min(v, ws_cand<PLAT>(V[ip + 1]));
+        if (v != o) { V[i] = v; ch = true; }
+        up = v;
+    }
+    return ch;
+}
+
+template <bool PLAT>
+__device__ bool ws_sweep_set(int *V, const uint8_t *E) {
+    const int t = threadIdx.x;
+    bool ch = false;
+    if (t < TS) {
+        ch |= ws_row_pass<+1, PLAT>(V, E, t + 1);
+        ch |= ws_row_pass<-1, PLAT>(V, E, t + 1);
+    }
+    __syncthreads();
+    if (t < TS) {
+        ch |= ws_column_pass<+1, PLAT>(V, E, t);
+        ch |= ws_column_pass<-1, PLAT>(V, E, t);
+    }
+    return __syncthreads_or(ch) != 0;
+}
+
+// One relaxation step over the interior (each pixel takes the least
+// candidate of its in-neighbours); the pixels it lowers are queued, after
+// which every pixel that can still lower a neighbour is queued.
+template <int NT, bool PLAT>
+__device__ unsigned ws_dilate_seed(int *V, const uint8_t *E, const RQ &q, const int *off) {
+    unsigned pushed = 0;
+    for (int base = 0; base < TS * TS; base += NT) {
+        const int k = base + threadIdx.x;
+        unsigned m = 0;
+        int i = 0;
+        if (k < TS * TS) {
+            const int r = k / TS + 1, c = k - (k / TS) * TS + 1;
+            i = gcell(r, c);
+            const unsigned e = E[gmask(r, c)];
+            if (e) {
+                const int o = V[i];
+                int v = o;
+#pragma unroll
+                for (int n = 0; n < 8; ++n)
+                    if (e & (1u << n)) v = min(v, ws_cand<PLAT>(V[i + off[n]]));
+                if (v < o) {
+                    V[i] = v;
+                    m = 1u << 8;
+                }
+            }
+        }
+        pushed += warp_enqueue(m, i, off, q);
+    }
+    return pushed;
+}
+
+// later visits: halo pixels that can lower an interior neighbour (the
+// neighbour's in-edge from the halo pixel is its mirror bit 7 - n)
+template <int NT, bool PLAT>
+__device__ unsigned ws_halo_seed(int *V, const uint8_t *E, const RQ &q, const int *off) {
+    unsigned pushed = 0;
+    for (int base = 0; base < 4 * (TS + 1); base += NT) {
+        const int k = base + threadIdx.x;
+        unsigned m = 0;
+        int i = 0;
+        if (k < 4 * (TS + 1)) {
+            int r, c;
+            halo_cell(k, r, c);
+            i = gcell(r, c);
+            const int cv = ws_cand<PLAT>(V[i]);
+#pragma unroll
+            for (int n = 0; n < 8; ++n) {
+                const int rr = r + nb_dy(8, n), cc = c + nb_dx(8, n);
+                if (rr >= 1 && rr <= TS && cc >= 1 && cc <= TS && (E[gmask(rr, cc)] & (1u << (7 - n))) &&
+                    cv < V[i + off[n]])
+                    m = 1u << 8;
+            }
+        }
+        pushed += warp_enqueue(m, i, off, q);
+    }
+    return pushed;
+}
+
+template <int NT, bool PLAT>
+__device__ bool ws_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, uint32_t &phase,
+                         unsigned long long deadline) {
+    constexpr int INF = WS_INF<PLAT>;
+    int *hdr = (int *)sm;
+    uint64_t *bar = (uint64_t *)(sm + 256);
+    int *V = (int *)(sm + G_D);
+    uint8_t *E = (uint8_t *)(sm + G_M);
+    uint16_t *Q0 = (uint16_t *)(sm + G_U), *Q1 = Q0 + QCAP_G;
+    const int tid = threadIdx.x;
+    const int lt = gt - jd->tile_base, tx = lt % jd->tiles_x, ty = lt / jd->tiles_x;
+    const int x0 = tx * TS, y0 = ty * TS;
+    int *out = (int *)jd->out;
+
+    PhaseClock pc;
+    pc.start();
+    load_sources(ka, jd, tx, ty, hdr);
+    begin_visit(hdr);
+    make_offsets<8, BI32_W>(hdr);
+    // 1. stage the in-edge masks (0 outside the image: no edges) and the
+    //    current values (the plane always holds valid values: the per-pixel
+    //    kernels initialised it)
+    __syncthreads();
+    const bool first = hdr[H_SRC + 4] == 0;
+    if (jd->use_tma) {
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, BU8_BYTES + BI32_BYTES);
+            tma_load_2d(E, &jd->tm[0], x0 - 16, y0 - 1, bar);
+            tma_load_2d(V, &jd->tm[2], x0 - 4, y0 - 1, bar);
+        }
+        if (!wait_boxes(bar, phase, deadline, ka.ctl)) return false;
+    } else {
+        stage_plain<uint8_t, BU8_W>(E, (const uint8_t *)jd->a, jd->pa, jd->h, jd->w, x0 - 16, y0 - 1, NT);
+        stage_plain<int, BI32_W>(V, out, jd->po, jd->h, jd->w, x0 - 4, y0 - 1, NT);
+        __syncthreads();
+    }
+    for (int i = tid; i < RR * RR; i += NT) {
+        const int r = i / RR, c = i - r * RR;
+        const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+        int v = INF;
+        if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
+            v = V[gcell(r, c)];
+            if (!PLAT && v == 0) v = INF;
+        }
+        V[gcell(r, c)] = v;
+    }
+    __syncthreads();
+    pc.mark(hdr, 0);
+    const int *off = hdr + H_OFF;
+
+    // 2. seeds: sweep sets then one relaxation step (first visit, or a
+    //    later visit whose halo changed in many places); else halo seeds
+    uint16_t *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
+    const int qcap = (ka.queue_mode & 2) ? 0 : QCAP_G;
+    RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, qcap, ka.spill_cap, ka.queue_mode & 1};
+    auto sweeps_then_seed = [&]() -> unsigned {
+        bool changed = true;
+        for (int s = 0; s < ka.ws_sweeps && changed; ++s) changed = ws_sweep_set<PLAT>(V, E);
+        if (!changed && ka.ws_sweeps > 0) return 0u;
+        return ws_dilate_seed<NT, PLAT>(V, E, q0, off);
+    };
+    unsigned seeds;
+    if (first) {
+        seeds = sweeps_then_seed();
+    } else {
+        seeds = ws_halo_seed<NT, PLAT>(V, E, q0, off);
+        __syncthreads();
+        if (hdr[H_CNT0] > ka.revisit_sweep_min) {
+            __syncthreads();
+            if (tid == 0) { hdr[H_CNT0] = 0; hdr[H_RESCAN] = 0; }
+            __syncthreads();
+            seeds = sweeps_then_seed();
+        }
+    }
+    if ((tid & 31) == 0) atomicAdd(hdr + H_SEEDS, (int)seeds);
+    pc.mark(hdr, 1);
+
+    // 3. propagation rounds (atomicMin along the in-edges of interior pixels)
+    auto proc = [&](int p, int n) -> bool {
+        const int pr = p / BI32_W, pcol = p - pr * BI32_W - 3;
+        const int rr = pr + nb_dy(8, n), cc = pcol + nb_dx(8, n);
+        if (rr < 1 || rr > TS || cc < 1 || cc > TS || !(E[gmask(rr, cc)] & (1u << (7 - n)))) return false;
+        const int cand = ws_cand<PLAT>(((volatile int *)V)[p]);
+        return atomicMin(V + p + off[n], cand) > cand;
+    };
+    auto rescan = [&](const RQ &q) -> unsigned { return ws_dilate_seed<NT, PLAT>(V, E, q, off); };
+    run_rounds<NT, 8>(hdr, Q0, Q1, qcap, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl,
+                      ka.queue_mode & 1);
+    __syncthreads();
+    pc.mark(hdr, 2);
+
+    // 4. store the interior (labels: INT_MAX back to 0); 16-byte stores
+    //    when the tile is whole and the plane meets TMA's alignment
+    if (jd->use_tma && x0 + TS <= jd->w) {
+        for (int i = tid; i < TS * TS / 4; i += NT) {
+            const int r = i / (TS / 4), c4 = i - r * (TS / 4);
+            const int gy = y0 + r;
+            if (gy >= jd->h) continue;
+            int4 v = *(const int4 *)(V + gcell(r + 1, 1 + 4 * c4));
+            if (!PLAT) {
+                v.x = v.x == INF ? 0 : v.x;
+                v.y = v.y == INF ? 0 : v.y;
+                v.z = v.z == INF ? 0 : v.z;
+                v.w = v.w == INF ? 0 : v.w;
+            }
+            *(int4 *)(out + (int64_t)gy * jd->po + x0 + 4 * c4) = v;
+        }
+    } else {
+        for (int i = tid; i < TS * TS; i += NT) {
+            const int r = i / TS, c = i - r * TS;
+            const int gy = y0 + r, gx = x0 + c;
+            if (gy >= jd->h || gx >= jd->w) continue;
+            const int v = V[gcell(r + 1, c + 1)];
+            out[(int64_t)gy * jd->po + gx] = (!PLAT && v == INF) ? 0 : v;
+        }
+    }
+    __syncthreads();
+    publish_tile(ka, gt, hdr);
+
+    // 5. border test: can an interior pixel lower a halo pixel's current
+    //    value along one of the halo pixel's in-edges?
+    for (int k = tid; k < 4 * (TS + 1); k += NT) {
+        int r, c;
+        halo_cell(k, r, c);
+        const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+        if (gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w) continue;
+        const unsigned e = E[gmask(r, c)];
+        if (!e) continue;
+        int cur = __ldcg(out + (int64_t)gy * jd->po + gx);
+        if (!PLAT && cur == 0) cur = INF;
+        bool need = false;
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            const int pr = r + nb_dy(8, n), pcc = c + nb_dx(8, n);
+            if (pr < 1 || pr > TS || pcc < 1 || pcc > TS || !(e & (1u << n))) continue;
+            if (ws_cand<PLAT>(V[gcell(pr, pcc)]) < cur) need = true;
+        }
+        if (need) hdr[H_FLAG + region(r) * 3 + region(c)] = 1;
+    }
+    __syncthreads();
+    finish_tile(ka, jd, gt, tx, ty, hdr);
+    pc.mark(hdr, 3);
+    return true;
+}
+
+// =====================================================================
 // kernels
 // =====================================================================
 
@@ -1688,6 +1978,10 @@ __global__ void __launch_bounds__(FAM_NT[FAM], FAM_MINB[FAM]) persistent_kernel(
             }
             if constexpr (FAM == FAM_GDT) {
                 if (jd->op == OP_GDT) ok = gdt_visit<NT>(ka, jd, t, smem, phase, deadline);
+            }
+            if constexpr (FAM == FAM_WS) {
+                if (jd->op == OP_WS_DIST) ok = ws_visit<NT, true>(ka, jd, t, smem, phase, deadline);
+                else if (jd->op == OP_WS_LABEL) ok = ws_visit<NT, false>(ka, jd, t, smem, phase, deadline);
             }
         }
         if (!ok) break;  // timeout raised; the host reports it
@@ -1805,6 +2099,7 @@ cudaError_t family_occupancy(int fam, int *n) {
         case FAM_EDT: return occ<FAM_EDT>(n);
         case FAM_MIXED: return occ<FAM_MIXED>(n);
         case FAM_GDT: return occ<FAM_GDT>(n);
+        case FAM_WS: return occ<FAM_WS>(n);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1833,6 +2128,7 @@ cudaError_t launch_persistent(const KArgs &ka, int fam, int grid, cudaStream_t s
         case FAM_EDT: launch_fam<FAM_EDT>(ka, grid, s); break;
         case FAM_MIXED: launch_fam<FAM_MIXED>(ka, grid, s); break;
         case FAM_GDT: launch_fam<FAM_GDT>(ka, grid, s); break;
+        case FAM_WS: launch_fam<FAM_WS>(ka, grid, s); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -286,3 +286,17 @@ def apply_tissue(marker: np.ndarray, mask: np.ndarray, region: np.ndarray):
     """(marker, mask) with everything outside the tissue region set to 0."""
     return marker * region.astype(marker.dtype), mask * region.astype(mask.dtype)
 
+
+
+def grid_markers(h: int, w: int, spacing: int, seed: int) -> np.ndarray:
+    """Watershed markers: the image is cut into spacing x spacing cells and
+    each cell gets one marker pixel at a uniformly drawn position inside it
+    (clipped to the image), labelled 1, 2, ... in row-major cell order;
+    int32, 0 elsewhere."""
+    rng = np.random.default_rng(seed)
+    gy, gx = np.meshgrid(np.arange(0, h, spacing), np.arange(0, w, spacing), indexing="ij")
+    py = np.minimum(gy + rng.integers(0, spacing, gy.shape), h - 1).ravel()
+    px = np.minimum(gx + rng.integers(0, spacing, gx.shape), w - 1).ravel()
+    m = np.zeros((h, w), np.int32)
+    m[py, px] = np.arange(1, py.size + 1, dtype=np.int32)
+    return m

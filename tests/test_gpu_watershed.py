@@ -1,0 +1,158 @@
+"""Watershed from markers (iwpp_watershed), the IWPP use of Section 1, on the
+GPU through the C ABI against the oracle (Dijkstra flooding, breadth-first
+plateau distances, per-label search): labels and flooding levels are
+unique, so every comparison is bit-exact -- uint8 and int32 reliefs of
+ragged sizes spanning many tiles, reliefs with few levels (wide plateaus
+crossing tile borders), a serpentine plateau, constant reliefs, pitched and
+unaligned inputs, degenerate cases and every sweep / queue setting."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1209_3314_gb300 import IWPPError, synth
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+IMAX = np.iinfo(np.int32).max
+
+
+def run(ctx, relief, markers, **opts):
+    if opts:
+        old = ctx.options()
+        ctx.set_options(**opts)
+    try:
+        f = torch.from_numpy(np.ascontiguousarray(relief)).to(DEV)
+        m = torch.from_numpy(np.ascontiguousarray(markers)).to(DEV)
+        lab, lev = ctx.watershed(f, m, with_levels=True)
+        torch.cuda.synchronize()
+        return lab.cpu().numpy(), lev.cpu().numpy()
+    finally:
+        if opts:
+            ctx.set_options(**old)
+
+
+def random_markers(rng, h, w, k, labels=50):
+    m = np.zeros((h, w), np.int32)
+    m[rng.integers(0, h, k), rng.integers(0, w, k)] = rng.integers(1, labels + 1, k)
+    return m
+
+
+def check(ctx, relief, markers, **opts):
+    lab, lev = run(ctx, relief, markers, **opts)
+    elab, elev = oracle.watershed(relief, markers)
+    np.testing.assert_array_equal(lev, elev)
+    np.testing.assert_array_equal(lab, elab)
+
+
+@pytest.mark.parametrize("levels", [2, 5, 256])
+def test_small_random_u8(cuda_ctx, levels):
+    rng = np.random.default_rng(100 + levels)
+    for _ in range(25):
+        h, w = (int(v) for v in rng.integers(1, 230, 2))
+        f = rng.integers(0, levels, (h, w)).astype(np.uint8)
+        check(cuda_ctx, f, random_markers(rng, h, w, int(rng.integers(1, 12))))
+
+
+def test_blurred_relief_ragged(cuda_ctx):
+    for k, (h, w) in enumerate(((333, 517), (64, 64), (65, 129), (1, 700), (700, 1), (257, 255))):
+        f = synth.blurred_noise_u8(h, w, 4.0, 110 + k)
+        check(cuda_ctx, f, synth.grid_markers(h, w, 37, 120 + k))
+
+
+def test_int32_relief(cuda_ctx):
+    rng = np.random.default_rng(130)
+    for _ in range(10):
+        h, w = (int(v) for v in rng.integers(1, 200, 2))
+        f = rng.choice(np.array([np.iinfo(np.int32).min, -7, 0, 3, 1 << 20, IMAX], np.int32), (h, w))
+        check(cuda_ctx, f, random_markers(rng, h, w, int(rng.integers(1, 8)), labels=1 << 30))
+    f = (synth.blurred_noise_u8(300, 280, 3.0, 131).astype(np.int32) - 128) * 1000003
+    check(cuda_ctx, f, synth.grid_markers(300, 280, 25, 132))
+
+
+def test_constant_relief_plateau_across_tiles(cuda_ctx):
+    rng = np.random.default_rng(140)
+    f = np.full((300, 410), 17, np.uint8)
+    check(cuda_ctx, f, random_markers(rng, 300, 410, 7, labels=4))
+    # a single marker: one label, and the plateau spans every tile
+    m = np.zeros((300, 410), np.int32)
+    m[299, 0] = 9
+    lab, lev = run(cuda_ctx, f, m)
+    assert (lab == 9).all() and (lev == 17).all()
+
+
+def test_serpentine_plateau(cuda_ctx):
+    # low corridors (value 10) behind high walls (200) that open at
+    # alternating ends: one winding plateau whose breadth-first distance
+    # crosses every tile row many times; markers at both ends of the path
+    h, w = 260, 200
+    f = np.full((h, w), 10, np.uint8)
+    for k, r in enumerate(range(5, h, 5)):
+        f[r, :] = 200
+        if k % 2 == 0:
+            f[r, w - 2:] = 10
+        else:
+            f[r, :2] = 10
+    m = np.zeros((h, w), np.int32)
+    m[0, 0] = 1
+    m[h - 1, 0 if len(range(5, h, 5)) % 2 == 1 else w - 1] = 2  # the far end of the path
+    check(cuda_ctx, f, m)
+
+
+def test_pitched_and_unaligned(cuda_ctx):
+    rng = np.random.default_rng(150)
+    big = synth.blurred_noise_u8(301, 333, 3.0, 151)
+    bigm = random_markers(rng, 301, 333, 40)
+    f = torch.from_numpy(big).to(DEV)[1:, 3:330]  # odd offset: plain staging
+    m = torch.from_numpy(bigm).to(DEV)[1:, 3:330]
+    lab, lev = cuda_ctx.watershed(f, m, with_levels=True)
+    elab, elev = oracle.watershed(big[1:, 3:330].copy(), bigm[1:, 3:330].copy())
+    np.testing.assert_array_equal(lev.cpu().numpy(), elev)
+    np.testing.assert_array_equal(lab.cpu().numpy(), elab)
+    # labels only (no levels output)
+    lab2 = cuda_ctx.watershed(f, m)
+    np.testing.assert_array_equal(lab2.cpu().numpy(), elab)
+
+
+def test_degenerate(cuda_ctx):
+    f = synth.blurred_noise_u8(90, 70, 2.0, 160)
+    lab, lev = run(cuda_ctx, f, np.zeros((90, 70), np.int32))
+    assert (lab == 0).all() and (lev == 255).all()
+    lab, lev = run(cuda_ctx, f.astype(np.int32), np.zeros((90, 70), np.int32))
+    assert (lab == 0).all() and (lev == IMAX).all()
+    check(cuda_ctx, np.array([[3]], np.uint8), np.array([[5]], np.int32))
+    every = np.arange(1, 90 * 70 + 1, dtype=np.int32).reshape(90, 70)
+    lab, lev = run(cuda_ctx, f, every)
+    np.testing.assert_array_equal(lab, every)
+    np.testing.assert_array_equal(lev, f)
+    # negative labels are labels too
+    rng = np.random.default_rng(161)
+    m = random_markers(rng, 90, 70, 9) - 30
+    m[m == -30] = 0
+    check(cuda_ctx, f, m)
+
+
+@pytest.mark.parametrize("opts", [dict(ws_sweeps=0), dict(ws_sweeps=1), dict(ws_sweeps=16),
+                                  dict(queue_mode=1), dict(queue_mode=2), dict(queue_mode=3),
+                                  dict(spill_cap=0), dict(blocks_per_sm=1)])
+def test_settings(cuda_ctx, opts):
+    f = synth.blurred_noise_u8(400, 380, 3.0, 170)
+    f = (f // 16).astype(np.uint8)  # 16 levels: wide plateaus
+    check(cuda_ctx, f, synth.grid_markers(400, 380, 45, 171), **opts)
+
+
+def test_invalid_arguments(cuda_ctx):
+    f = torch.zeros((10, 10), dtype=torch.uint8, device=DEV)
+    m = torch.zeros((10, 10), dtype=torch.int32, device=DEV)
+    with pytest.raises(IWPPError):
+        cuda_ctx.watershed(f, m.to(torch.uint8))
+    with pytest.raises(IWPPError):
+        cuda_ctx.watershed(f, torch.zeros((10, 11), dtype=torch.int32, device=DEV))
+    with pytest.raises(IWPPError):
+        cuda_ctx.watershed(f, m, labels=m)  # labels alias the markers
+
+
+@pytest.mark.slow
+def test_4096_blurred(cuda_ctx):
+    f = synth.blurred_noise_u8(4096, 4096, 8.0, 180)
+    check(cuda_ctx, f, synth.grid_markers(4096, 4096, 64, 181))
