@@ -534,6 +534,60 @@ def bench_geodesic(ctx, dev, side, reps=3):
     return res
 
 
+def bench_watershed(ctx, dev, d_relief, side, reps=3, cpu_sample=2048):
+    """Watershed from markers (iwpp_watershed) on the reconstruction's relief
+    (16384^2 blurred noise, uint8, and the same values as int32) with one
+    marker per 64x64 cell at a random position (65,536 labels): per-call
+    CUDA-event times (median) of the whole call -- three per-pixel kernels
+    and three propagations -- with the levels written too; the compulsory
+    traffic is relief + markers in, labels + levels out.  The oracle is
+    timed on a cpu_sample^2 crop, one thread."""
+    import statistics
+    import time
+
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1209_3314_gb300 import synth
+
+    mk = synth.grid_markers(side, side, 64, 5100)
+    d_mk = torch.from_numpy(mk).to(dev)
+    st = torch.cuda.current_stream(dev)
+    labels = torch.empty((side, side), dtype=torch.int32, device=dev)
+    res = {"workload": f"{side}x{side} relief (blurred noise, sigma 16), one marker per 64x64 cell "
+                       f"({int((mk != 0).sum())} labels), 8-connected"}
+    for name, rel in (("u8", d_relief), ("i32", d_relief.to(torch.int32))):
+        levels = torch.empty_like(rel)
+        ctx.watershed(rel, d_mk, labels=labels, levels=levels)
+        ctx.stats_reset()
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            ctx.watershed(rel, d_mk, labels=labels, levels=levels)
+            b.record(st)
+            torch.cuda.synchronize(dev)
+            times.append(a.elapsed_time(b))
+        q = ctx.stats()
+        ms_ = statistics.median(times)
+        es = rel.element_size()
+        compulsory = side * side * (2 * es + 8)
+        res[name] = {"ms": round(ms_, 3), "mpx_s": round(side * side / ms_ / 1e3, 1),
+                     "compulsory_gbs": round(compulsory / (ms_ * 1e-3) / 1e9, 1),
+                     "tiles_per_call": q["tiles_processed"] // reps}
+        del levels, rel
+    if cpu_sample:
+        s = min(cpu_sample, side)
+        f = d_relief[:s, :s].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.watershed(f, np.ascontiguousarray(mk[:s, :s]))
+        t = time.perf_counter() - t0
+        res["cpu_oracle"] = {"mpx_s": round(s * s / t / 1e6, 3), "cores": 1,
+                             "sample": f"top-left {s}x{s} crop, uint8 relief"}
+    return res
+
+
 def run_gpu(args, ws, rank, local):
     import numpy as np
     import torch
@@ -713,6 +767,9 @@ def run_gpu(args, ws, rank, local):
     geodesic = None
     if rank == 0 and not args.skip_geodesic:
         geodesic = bench_geodesic(ctx, dev, side)
+    watershed = None
+    if rank == 0 and not args.skip_watershed:
+        watershed = bench_watershed(ctx, dev, d_mask, side, cpu_sample=0 if args.no_cpu_baseline else 2048)
     exact = None
     if rank == 0 and not args.skip_exact:
         exact = bench_edt_exact(ctx, dev, d_bin, npx)
@@ -756,6 +813,7 @@ def run_gpu(args, ws, rank, local):
             "edt_exact": exact,
             "coverage": coverage,
             "geodesic": geodesic,
+            "watershed": watershed,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_val, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3), "check": ok},
@@ -783,6 +841,7 @@ def main():
     ap.add_argument("--skip-exact", action="store_true")
     ap.add_argument("--skip-coverage", action="store_true")
     ap.add_argument("--skip-geodesic", action="store_true")
+    ap.add_argument("--skip-watershed", action="store_true")
     ap.add_argument("--batch-images", type=int, default=512)
     ap.add_argument("--serve-rates", default="200,500,1000,2000")
     ap.add_argument("--serve-duration", type=float, default=1.0)

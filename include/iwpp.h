@@ -86,7 +86,7 @@ typedef struct {
  * sweeps 3, queue_factor 32, spill_cap 8192, max_relaunch 1, timeout_ms
  * 10000, timing 0, revisit_sweep_min 0, edt_sweeps 2, edt_revisit_sweep_min
  * 64, revisit_sweeps -1, queue_mode 0, test_empty_slot 0, gdt_sweeps 8,
- * batch_split 1, ws_sweeps 4.  tile = 0 lets the autotuner choose.  Values are validated
+ * batch_split 1, ws_sweeps 2.  tile = 0 lets the autotuner choose.  Values are validated
  * by iwpp_set_options().  New fields are only ever appended. */
 typedef struct {
     int32_t tile;            /* tile side in pixels: 0 (auto) or 64           */

@@ -648,7 +648,7 @@ int iwpp_ctx_create(iwpp_ctx **out, int device, size_t hbm_budget_bytes) {
     ctx->opt.revisit_sweeps = -1;
     ctx->opt.gdt_sweeps = 8;
     ctx->opt.batch_split = 1;
-    ctx->opt.ws_sweeps = 4;
+    ctx->opt.ws_sweeps = 2;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&ctx->ctl, sizeof(Control)) != cudaSuccess ||
@@ -792,7 +792,8 @@ int iwpp_watershed(iwpp_ctx *ctx, const iwpp_image *relief, const iwpp_image *ma
     CK(launch_ws_label_init(a, st), "watershed label init launch");
     std::vector<JobDesc> j3{ws_job(OP_WS_LABEL, h, w, a.E, labels)};
     if ((rc = run(ctx, j3, st, false))) return rc;
-    ctx->launches += 3;
+    CK(launch_ws_label_finish(a, st), "watershed label finish launch");
+    ctx->launches += 4;
     ctx->calls -= 2;  // the three propagations are one call
     return iwpp_sync(ctx, st);
 }

@@ -102,6 +102,7 @@ struct WsArgs {
 cudaError_t launch_ws_complement(const WsArgs &a, cudaStream_t s);
 cudaError_t launch_ws_plateau_init(const WsArgs &a, cudaStream_t s);
 cudaError_t launch_ws_label_init(const WsArgs &a, cudaStream_t s);
+cudaError_t launch_ws_label_finish(const WsArgs &a, cudaStream_t s);
 
 // Launch helpers implemented in iwpp_kernels.cu.
 int family_threads(int fam);

@@ -1017,24 +1017,35 @@ struct Pick {
 // Row pass of the distance-transform sweep (one thread per row, DIR +1
 // left to right, -1 right to left): each pixel keeps the better of its own
 // feature and the previous pixel's, as Danielsson's raster vector
-// propagation does.
+// propagation does.  The features are read four cells at a time with
+// 16-byte loads (cell 1 sits at word r*72 + 4): the threads of a warp own
+// rows 72 words apart, which scalar loads would put on 4 banks.  Only the
+// cells a pass improves are stored.
 template <int DIR>
 __device__ __forceinline__ bool edt_row_pass(unsigned *__restrict__ V, int r, int oy, int ox) {
     const int base = r * EP + 3, y = oy + r;
+    const uint4 *vp = (const uint4 *)(V + base + 1);
     bool ch = false;
     unsigned run = V[base + (DIR > 0 ? 0 : TS + 1)];
-#pragma unroll 4
-    for (int s = 1; s <= TS; ++s) {
-        const int c = DIR > 0 ? s : TS + 1 - s;
-        const unsigned f = V[base + c];
-        if (f == pack_yx(y, ox + c)) {  // a feature is its own nearest
-            run = f;
-            continue;
+#pragma unroll 1
+    for (int s = 0; s < TS / 4; ++s) {
+        const int k = DIR > 0 ? s : TS / 4 - 1 - s;
+        const uint4 q = vp[k];
+        const unsigned f4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int jj = DIR > 0 ? j : 3 - j;
+            const int c = 4 * k + jj + 1;
+            const unsigned f = f4[jj];
+            if (f == pack_yx(y, ox + c)) {  // a feature is its own nearest
+                run = f;
+                continue;
+            }
+            Pick p(f, y, ox + c);
+            p.consider(run, y, ox + c);
+            if (p.best != f) { V[base + c] = p.best; ch = true; }
+            run = p.best;
         }
-        Pick p(f, y, ox + c);
-        p.consider(run, y, ox + c);
-        if (p.best != f) { V[base + c] = p.best; ch = true; }
-        run = p.best;
     }
     return ch;
 }
@@ -1385,20 +1396,55 @@ __device__ __forceinline__ int gcell(int r, int c) { return r * BI32_W + c + 3; 
 __device__ __forceinline__ int gmask(int r, int c) { return r * BU8_W + c + 15; }
 __device__ __forceinline__ int gstep(int n) { return (nb_dy(8, n) != 0 && nb_dx(8, n) != 0) ? 7 : 5; }
 
-template <int DIR>
-__device__ __forceinline__ bool gdt_row_pass(int *__restrict__ D, const uint8_t *__restrict__ M, int r) {
-    const int base = gcell(r, 0), mb = gmask(r, 0);
-    int run = D[base + (DIR > 0 ? 0 : TS + 1)];
+// Row pass (one thread per row) over an int32 working row and its uint8
+// companion row (mask / in-edge bits): the 64 interior cells of both are
+// 16-byte aligned (int32 cell 1 at word r*72 + 4, uint8 cell 1 at byte
+// r*96 + 16), so each 16-cell chunk comes with four int4 and one uint4
+// shared loads, is worked on in registers and is stored back by the int4
+// that changed.  Threads of a warp own rows 72 words apart, so scalar
+// accesses would fall on 4 banks; 16-byte ones spread over them.
+// relax(run, old, byte) gives a cell's new value.
+template <int DIR, typename Relax>
+__device__ __forceinline__ bool i32_u8_row_pass(int *__restrict__ V, const uint8_t *__restrict__ M, int r,
+                                                Relax relax) {
+    int4 *vp = (int4 *)(V + gcell(r, 1));
+    const uint4 *mp = (const uint4 *)(M + gmask(r, 1));
+    int run = V[gcell(r, DIR > 0 ? 0 : TS + 1)];
     bool ch = false;
-#pragma unroll 4
-    for (int s = 1; s <= TS; ++s) {
-        const int c = DIR > 0 ? s : TS + 1 - s;
-        const int o = D[base + c];
-        const int v = M[mb + c] ? min(o, run + 5) : o;
-        if (v != o) { D[base + c] = v; ch = true; }
-        run = v;
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) {
+        const int k = DIR > 0 ? s : 3 - s;
+        const uint4 mw = mp[k];
+        const uint32_t m[4] = {mw.x, mw.y, mw.z, mw.w};
+        int v[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int4 a = vp[4 * k + q];
+            v[4 * q] = a.x;
+            v[4 * q + 1] = a.y;
+            v[4 * q + 2] = a.z;
+            v[4 * q + 3] = a.w;
+        }
+        unsigned changed = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int c = DIR > 0 ? j : 15 - j;
+            const int nv = relax(run, v[c], (m[c >> 2] >> (8 * (c & 3))) & 0xFFu);
+            changed |= (nv != v[c] ? 1u : 0u) << (c >> 2);
+            v[c] = nv;
+            run = nv;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (changed & (1u << q)) vp[4 * k + q] = make_int4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        ch |= changed != 0;
     }
     return ch;
+}
+
+template <int DIR>
+__device__ __forceinline__ bool gdt_row_pass(int *__restrict__ D, const uint8_t *__restrict__ M, int r) {
+    return i32_u8_row_pass<DIR>(D, M, r, [](int run, int o, unsigned m) { return m ? min(o, run + 5) : o; });
 }
 
 // column pass; the diagonal neighbours of the previous row are read from
@@ -1653,14 +1699,13 @@ __device__ bool gdt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
 //     neighbours of equal level; entry pixels start at 0, the rest at
 //     WS_DINF;
 //   labels: V(q) = min(V(q), V(p)) over the optimal edges; marker pixels
-//     have no in-edges and keep their value; 0 (no label) is held as
-//     INT_MAX while the tile is staged.
+//     have no in-edges and keep their value; a pixel without a label holds
+//     INT_MAX until the last per-pixel kernel writes 0 there.
 // Wavefront element: a pixel whose value can lower an out-neighbour.  The
 // sweeps, seeding, queue rounds and border test follow the shortest-path
-// family with the edge mask in place of the obstacle mask.
-
-template <bool PLAT>
-constexpr int WS_INF = PLAT ? WS_DINF : INT_MAX;
+// family with the edge mask in place of the obstacle mask.  Pixels outside
+// the image are never an in-neighbour (their bits are 0 in every mask), so
+// the staged boxes need no fill values: the halo is used as loaded.
 
 template <bool PLAT>
 __device__ __forceinline__ int ws_cand(int v) { return PLAT ? v + 1 : v; }
@@ -1668,18 +1713,9 @@ __device__ __forceinline__ int ws_cand(int v) { return PLAT ? v + 1 : v; }
 template <int DIR, bool PLAT>
 __device__ __forceinline__ bool ws_row_pass(int *__restrict__ V, const uint8_t *__restrict__ E, int r) {
     constexpr unsigned FROM = DIR > 0 ? 1u << 3 : 1u << 4;  // the left / right neighbour
-    const int base = gcell(r, 0), eb = gmask(r, 0);
-    int run = V[base + (DIR > 0 ? 0 : TS + 1)];
-    bool ch = false;
-#pragma unroll 4
-    for (int s = 1; s <= TS; ++s) {
-        const int c = DIR > 0 ? s : TS + 1 - s;
-        const int o = V[base + c];
-        const int v = (E[eb + c] & FROM) ? min(o, ws_cand<PLAT>(run)) : o;
-        if (v != o) { V[base + c] = v; ch = true; }
-        run = v;
-    }
-    return ch;
+    return i32_u8_row_pass<DIR>(V, E, r, [](int run, int o, unsigned e) {
+        return (e & FROM) ? min(o, ws_cand<PLAT>(run)) : o;
+    });
 }
 
 // column pass; the diagonal neighbours of the previous row are read from
@@ -1786,7 +1822,6 @@ __device__ unsigned ws_halo_seed(int *V, const uint8_t *E, const RQ &q, const in
 template <int NT, bool PLAT>
 __device__ bool ws_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, uint32_t &phase,
                          unsigned long long deadline) {
-    constexpr int INF = WS_INF<PLAT>;
     int *hdr = (int *)sm;
     uint64_t *bar = (uint64_t *)(sm + 256);
     int *V = (int *)(sm + G_D);
@@ -1804,7 +1839,8 @@ __device__ bool ws_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, u
     make_offsets<8, BI32_W>(hdr);
     // 1. stage the in-edge masks (0 outside the image: no edges) and the
     //    current values (the plane always holds valid values: the per-pixel
-    //    kernels initialised it)
+    //    kernels initialised it; values outside the image are never read as
+    //    candidates)
     __syncthreads();
     const bool first = hdr[H_SRC + 4] == 0;
     if (jd->use_tma) {
@@ -1820,17 +1856,6 @@ __device__ bool ws_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, u
         stage_plain<int, BI32_W>(V, out, jd->po, jd->h, jd->w, x0 - 4, y0 - 1, NT);
         __syncthreads();
     }
-    for (int i = tid; i < RR * RR; i += NT) {
-        const int r = i / RR, c = i - r * RR;
-        const int gy = y0 - 1 + r, gx = x0 - 1 + c;
-        int v = INF;
-        if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
-            v = V[gcell(r, c)];
-            if (!PLAT && v == 0) v = INF;
-        }
-        V[gcell(r, c)] = v;
-    }
-    __syncthreads();
     pc.mark(hdr, 0);
     const int *off = hdr + H_OFF;
 
@@ -1875,29 +1900,21 @@ __device__ bool ws_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, u
     __syncthreads();
     pc.mark(hdr, 2);
 
-    // 4. store the interior (labels: INT_MAX back to 0); 16-byte stores
-    //    when the tile is whole and the plane meets TMA's alignment
+    // 4. store the interior; 16-byte stores when the tile is whole and the
+    //    plane meets TMA's alignment
     if (jd->use_tma && x0 + TS <= jd->w) {
         for (int i = tid; i < TS * TS / 4; i += NT) {
             const int r = i / (TS / 4), c4 = i - r * (TS / 4);
             const int gy = y0 + r;
             if (gy >= jd->h) continue;
-            int4 v = *(const int4 *)(V + gcell(r + 1, 1 + 4 * c4));
-            if (!PLAT) {
-                v.x = v.x == INF ? 0 : v.x;
-                v.y = v.y == INF ? 0 : v.y;
-                v.z = v.z == INF ? 0 : v.z;
-                v.w = v.w == INF ? 0 : v.w;
-            }
-            *(int4 *)(out + (int64_t)gy * jd->po + x0 + 4 * c4) = v;
+            *(int4 *)(out + (int64_t)gy * jd->po + x0 + 4 * c4) = *(const int4 *)(V + gcell(r + 1, 1 + 4 * c4));
         }
     } else {
         for (int i = tid; i < TS * TS; i += NT) {
             const int r = i / TS, c = i - r * TS;
             const int gy = y0 + r, gx = x0 + c;
             if (gy >= jd->h || gx >= jd->w) continue;
-            const int v = V[gcell(r + 1, c + 1)];
-            out[(int64_t)gy * jd->po + gx] = (!PLAT && v == INF) ? 0 : v;
+            out[(int64_t)gy * jd->po + gx] = V[gcell(r + 1, c + 1)];
         }
     }
     __syncthreads();
@@ -1912,8 +1929,7 @@ __device__ bool ws_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, u
         if (gy < 0 || gy >= jd->h || gx < 0 || gx >= jd->w) continue;
         const unsigned e = E[gmask(r, c)];
         if (!e) continue;
-        int cur = __ldcg(out + (int64_t)gy * jd->po + gx);
-        if (!PLAT && cur == 0) cur = INF;
+        const int cur = __ldcg(out + (int64_t)gy * jd->po + gx);
         bool need = false;
 #pragma unroll
         for (int n = 0; n < 8; ++n) {
