@@ -156,3 +156,62 @@ def test_invalid_arguments(cuda_ctx):
 def test_4096_blurred(cuda_ctx):
     f = synth.blurred_noise_u8(4096, 4096, 8.0, 180)
     check(cuda_ctx, f, synth.grid_markers(4096, 4096, 64, 181))
+
+
+def _shift(x, dy, dx, fill):
+    """out[y, x] = x[y + dy, x + dx]; fill outside the image."""
+    h, w = x.shape
+    out = torch.full_like(x, fill)
+    out[max(-dy, 0):h + min(-dy, 0), max(-dx, 0):w + min(-dx, 0)] = \
+        x[max(dy, 0):h + min(dy, 0), max(dx, 0):w + min(dx, 0)]
+    return out
+
+
+OFF8 = [(dy, dx) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if dy or dx]
+
+
+@pytest.mark.slow
+def test_16384_certificates(cuda_ctx):
+    """Full size, the bench's workload shape (16384^2 blurred relief, one
+    marker per 64x64 cell), through certificates that have one solution
+    each, checked with torch on the device:
+    - levels: level = relief at markers, and elsewhere level = max(relief,
+      least neighbour level), whose only solution is the flooding level;
+    - plateau distances, computed here by Jacobi iteration: 0 at entry
+      pixels, else 1 + least equal-level neighbour distance;
+    - labels: markers keep theirs, every other pixel holds the least label
+      of its optimal in-neighbours (the optimal edges raise (level,
+      plateau distance), so this recursion has one solution)."""
+    side = 16384
+    f = torch.from_numpy(synth.blurred_noise_u8(side, side, 16.0, 190)).to(DEV)
+    m = torch.from_numpy(synth.grid_markers(side, side, 64, 191)).to(DEV)
+    lab, lev = cuda_ctx.watershed(f, m, with_levels=True)
+    torch.cuda.synchronize()
+    big = 1 << 30
+    c, fi, mk = lev.to(torch.int32), f.to(torch.int32), m != 0
+    del lev
+    assert bool((c >= fi).all()) and bool((c[mk] == fi[mk]).all())
+    least = torch.full_like(c, big)
+    for dy, dx in OFF8:
+        torch.minimum(least, _shift(c, dy, dx, big), out=least)
+    assert bool((c == torch.where(mk, fi, torch.maximum(fi, least))).all())
+    entry = mk | (least < c)
+    del least, fi
+    d = torch.where(entry, 0, big).to(torch.int32)
+    same = [_shift(c, dy, dx, -1) == c for dy, dx in OFF8]
+    for _ in range(side * side):
+        best = d.clone()
+        for (dy, dx), s in zip(OFF8, same):
+            torch.minimum(best, torch.where(s, _shift(d, dy, dx, big) + 1, big), out=best)
+        if torch.equal(best, d):
+            break
+        d = best
+    del same
+    assert int(d.max()) < big  # every pixel reached
+    want = torch.full_like(lab, np.iinfo(np.int32).max)
+    for dy, dx in OFF8:
+        nc = _shift(c, dy, dx, big)
+        opt = ((nc < c) & (d == 0)) | ((nc == c) & (_shift(d, dy, dx, -2) + 1 == d))
+        torch.minimum(want, torch.where(opt, _shift(lab, dy, dx, 0), np.iinfo(np.int32).max), out=want)
+    want = torch.where(mk, m, want)
+    assert torch.equal(lab, want)
