@@ -22,6 +22,9 @@ What it provides (paper = Teodoro et al., arXiv:1209.3314):
   minimum squared distance to any feature pixel.
 * ``gdt`` / ``gdt_bellman_ford`` -- shortest paths on a grid with obstacles
   (Section 1): Dijkstra's algorithm, and plain relaxation to a fixpoint.
+* ``skiz`` / ``skiz_per_label`` -- influence zones and their skeleton of
+  labelled sources inside a mask (Section 1), with the shortest-path metric
+  above: sequential C, and a restatement from one distance map per label.
 * ``watershed`` -- marker-controlled watershed by flooding (Section 1), the
   image foresting transform with the highest-value path cost, sequential C;
   ``watershed_levels_threshold`` / ``watershed_pdist_relax`` /
@@ -61,6 +64,7 @@ def _load():
         lib.oracle_edt_exact.argtypes = [i32, i32, vp, i32, vp]
         lib.oracle_gdt.argtypes = [i32, i32, vp, vp, vp, i64p]
         lib.oracle_watershed.argtypes = [i32, i32, vp, vp, vp, vp, vp, i64p]
+        lib.oracle_skiz.argtypes = [i32, i32, vp, vp, vp, vp, vp]
         for f in ("oracle_fh_i32", "oracle_fh_u8", "oracle_edt",
                   "oracle_edt_policy", "oracle_edt_exact"):
             getattr(lib, f).restype = ctypes.c_int
@@ -206,6 +210,51 @@ def watershed(relief: np.ndarray, markers: np.ndarray, stats: dict | None = None
     if f.dtype == np.uint8:
         level = np.minimum(level, 255).astype(np.uint8)
     return (label, level, pdist) if with_pdist else (label, level)
+
+
+def skiz(mask: np.ndarray, labels: np.ndarray):
+    """Influence zones of labelled sources (free pixels with labels != 0)
+    inside a mask (mask != 0 is free), with the shortest-path metric of
+    ``gdt``: returns (zones int32: the least label whose sources are
+    nearest, 0 at obstacles and unreachable pixels; skiz uint8: 1 where two
+    or more labels are nearest; dist int32 as ``gdt``)."""
+    lib = _load()
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    assert m.shape == lab.shape and m.ndim == 2
+    h, w = m.shape
+    zones = np.empty((h, w), np.int32)
+    sk = np.empty((h, w), np.uint8)
+    dist = np.empty((h, w), np.int32)
+    if lib.oracle_skiz(h, w, _ptr(m), _ptr(lab), _ptr(zones), _ptr(sk), _ptr(dist)) != 0:
+        raise MemoryError("oracle_skiz")
+    return zones, sk, dist
+
+
+def skiz_per_label(mask: np.ndarray, labels: np.ndarray):
+    """The same zones and skeleton from their definition: one distance map
+    per label (relaxation to a fixpoint, ``gdt_bellman_ford``); a label
+    reaches p when its map equals the least map at p.  Small images."""
+    m = np.asarray(mask) != 0
+    lab = np.asarray(labels).astype(np.int64)
+    IMAX = np.iinfo(np.int32).max
+    vals = np.unique(lab[m & (lab != 0)])
+    maps = [oracle_gdt_map(m, lab == L) for L in vals]
+    h, w = m.shape
+    if not maps:
+        return (np.zeros((h, w), np.int32), np.zeros((h, w), np.uint8),
+                np.full((h, w), IMAX, np.int32))
+    stack = np.stack(maps).astype(np.int64)
+    best = stack.min(axis=0)
+    reach = (stack == best) & (best < IMAX)
+    count = reach.sum(axis=0)
+    first = np.where(reach.any(axis=0), vals[np.argmax(reach, axis=0)], 0)
+    return first.astype(np.int32), (count >= 2).astype(np.uint8), best.astype(np.int32)
+
+
+def oracle_gdt_map(free: np.ndarray, sources: np.ndarray) -> np.ndarray:
+    """One label's distance map by relaxation (``gdt_bellman_ford``)."""
+    return gdt_bellman_ford(free.astype(np.uint8), sources.astype(np.uint8))
 
 
 def _shifted(a: np.ndarray, dy: int, dx: int, fill) -> np.ndarray:

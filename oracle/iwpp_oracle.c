@@ -22,6 +22,11 @@
  *   oracle_gdt                    Shortest-path (geodesic) distance on a grid
  *                                 with obstacles, one of the IWPP uses named
  *                                 in Section 1, by Dijkstra's algorithm.
+ *   oracle_skiz                   Influence zones and their skeleton (SKIZ)
+ *                                 of labelled sources inside a mask, another
+ *                                 IWPP use named in Section 1, by Dijkstra's
+ *                                 algorithm and breadth-first searches per
+ *                                 label along shortest-path edges.
  *   oracle_watershed              Marker-controlled watershed by flooding,
  *                                 another IWPP use named in Section 1:
  *                                 flooding levels by Dijkstra's algorithm on
@@ -594,4 +599,102 @@ int oracle_watershed(int h, int w, const int32_t *f, const int32_t *markers,
     free(hp); free(lv); free(pairs); free(done);
     if (stats) { stats[0] = pops; stats[1] = improv; stats[2] = ppush; stats[3] = lpush; }
     return 0;
+}
+
+/* ------------------------- influence zones and SKIZ (Section 1) */
+
+/*
+ * Influence zones of labelled sources inside a mask and their skeleton
+ * (SKIZ), named in Section 1 among the IWPP algorithms.  The paper defines
+ * neither; the definition taken here is the geodesic SKIZ (Lantuejoul,
+ * 1980) with the grid metric of oracle_gdt:
+ *   free(p)   = mask[p] != 0; sources: free pixels with labels[p] != 0;
+ *   dist[p]   = least cost of a path through free pixels from any source
+ *               (8 moves, cost 5 straight / 7 diagonal), as oracle_gdt;
+ *   a label L reaches p when the least cost from the sources labelled L
+ *               equals dist[p];
+ *   zones[p]  = the least label that reaches p (0 at obstacles and
+ *               unreachable pixels);
+ *   skiz[p]   = 1 when two or more labels reach p, else 0.
+ * A label reaches p exactly when p lies on a shortest path from one of its
+ * sources, i.e. along edges q -> p with dist[q] + cost = dist[p] (every
+ * prefix of a shortest path is shortest).  So: Dijkstra's algorithm for
+ * dist, then for each label value in increasing order a breadth-first
+ * search along such edges from its sources that marks the pixels not
+ * reached yet (the least label), and the same in decreasing order (the
+ * greatest); two labels reach p exactly when the two differ.
+ * Returns 0, or -1 on allocation failure.
+ */
+static void skiz_sweep(int h, int w, const uint8_t *mask, const int32_t *dist,
+                       const int64_t *pairs, int64_t np, int descending,
+                       int32_t *out, uint8_t *done, fifo_t *q) {
+    const int64_t n = (int64_t)h * w;
+    memset(done, 0, (size_t)n);
+    for (int64_t i = 0; i < np; i++) done[pairs[2 * i + 1]] = 1;
+    for (int64_t g = 0; g < np;) {
+        const int64_t a = descending ? np - 1 - g : g;
+        int64_t cnt = 0;
+        q->head = q->tail = 0;
+        while (g + cnt < np) {
+            const int64_t b = descending ? np - 1 - (g + cnt) : g + cnt;
+            if (pairs[2 * b] != pairs[2 * a]) break;
+            fifo_push(q, pairs[2 * b + 1]);
+            cnt++;
+        }
+        const int32_t L = (int32_t)pairs[2 * a];
+        while (q->head < q->tail) {
+            const int64_t p = fifo_pop(q, 0, NULL);
+            const int y = (int)(p / w), x = (int)(p % w);
+            for (int k = 0; k < 8; k++) {
+                const int qy = y + NB8[k][0], qx = x + NB8[k][1];
+                if (!inside(qy, qx, h, w)) continue;
+                const int64_t qq = (int64_t)qy * w + qx;
+                if (done[qq] || !mask[qq] || dist[qq] == INT32_MAX) continue;
+                const int64_t cost = (NB8[k][0] != 0 && NB8[k][1] != 0) ? 7 : 5;
+                if ((int64_t)dist[p] + cost == dist[qq]) {
+                    out[qq] = L;
+                    done[qq] = 1;
+                    fifo_push(q, qq);
+                }
+            }
+        }
+        g += cnt;
+    }
+}
+
+int oracle_skiz(int h, int w, const uint8_t *mask, const int32_t *labels,
+                int32_t *zones, uint8_t *skiz, int32_t *dist) {
+    const int64_t n = (int64_t)h * w;
+    uint8_t *seed = (uint8_t *)malloc((size_t)n + 1);
+    int32_t *zmax = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    uint8_t *done = (uint8_t *)malloc((size_t)n + 1);
+    int64_t np = 0;
+    for (int64_t i = 0; i < n; i++) np += mask[i] && labels[i];
+    int64_t *pairs = (int64_t *)malloc((size_t)(2 * np + 2) * sizeof(int64_t));
+    fifo_t q;
+    if (!seed || !zmax || !done || !pairs || fifo_init(&q, n + 1) != 0) {
+        free(seed); free(zmax); free(done); free(pairs);
+        return -1;
+    }
+    np = 0;
+    for (int64_t i = 0; i < n; i++) {
+        seed[i] = labels[i] != 0;
+        zones[i] = zmax[i] = 0;
+        if (mask[i] && labels[i]) {
+            zones[i] = zmax[i] = labels[i];
+            pairs[2 * np] = labels[i];
+            pairs[2 * np + 1] = i;
+            np++;
+        }
+    }
+    int rc = oracle_gdt(h, w, mask, seed, dist, NULL);
+    if (rc == 0) {
+        qsort(pairs, (size_t)np, 2 * sizeof(int64_t), cmp_pair);
+        skiz_sweep(h, w, mask, dist, pairs, np, 0, zones, done, &q);
+        skiz_sweep(h, w, mask, dist, pairs, np, 1, zmax, done, &q);
+        for (int64_t i = 0; i < n; i++) skiz[i] = zones[i] != zmax[i];
+    }
+    fifo_free(&q);
+    free(seed); free(zmax); free(done); free(pairs);
+    return rc;
 }

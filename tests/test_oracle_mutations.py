@@ -42,6 +42,12 @@ MUTATIONS = {
     "ws_flat_sideways": ("(int64_t)pdist[p] + 1 == pdist[qq];", "(int64_t)pdist[p] <= pdist[qq];"),
     "ws_largest_label_first": ("if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;",
                                "if (x[0] != y[0]) return x[0] < y[0] ? 1 : -1;"),
+    # influence zones / SKIZ (Section 1)
+    "skiz_any_shorter_edge": ("if ((int64_t)dist[p] + cost == dist[qq]) {", "if ((int64_t)dist[p] + cost >= dist[qq]) {"),
+    "skiz_swapped_costs": ("const int64_t cost = (NB8[k][0] != 0 && NB8[k][1] != 0) ? 7 : 5;\n                if ((int64_t)dist[p]",
+                           "const int64_t cost = (NB8[k][0] != 0 && NB8[k][1] != 0) ? 5 : 7;\n                if ((int64_t)dist[p]"),
+    "skiz_max_pass_ascending": ("skiz_sweep(h, w, mask, dist, pairs, np, 1, zmax, done, &q);",
+                                "skiz_sweep(h, w, mask, dist, pairs, np, 0, zmax, done, &q);"),
     "exact_separator_sign": ("int64_t num = (int64_t)u * u - i * i + gy[u] * gy[u] - gy[i] * gy[i];",
                              "int64_t num = (int64_t)u * u - i * i - gy[u] * gy[u] + gy[i] * gy[i];"),
 }
@@ -136,11 +142,32 @@ def _ws_pins_fail(lib):
     return False
 
 
+def _skiz_pins_fail(lib):
+    rng = np.random.default_rng(81)
+    for _ in range(120):
+        h, w = (int(v) for v in rng.integers(1, 16, 2))
+        m = (rng.random((h, w)) >= 0.25).astype(np.uint8)
+        lab = np.zeros((h, w), np.int32)
+        for _ in range(int(rng.integers(1, 6))):
+            lab[rng.integers(0, h), rng.integers(0, w)] = rng.integers(1, 5)
+        z, d = np.empty((h, w), np.int32), np.empty((h, w), np.int32)
+        s = np.empty((h, w), np.uint8)
+        vp = ctypes.c_void_p
+        lib.oracle_skiz(ctypes.c_int(h), ctypes.c_int(w), m.ctypes.data_as(vp), lab.ctypes.data_as(vp),
+                        z.ctypes.data_as(vp), s.ctypes.data_as(vp), d.ctypes.data_as(vp))
+        z2, s2, d2 = oracle.skiz_per_label(m, lab)
+        if not (np.array_equal(z, z2) and np.array_equal(s, s2) and np.array_equal(d, d2)):
+            return True
+    return False
+
+
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_is_caught(tmp_path, name):
     lib = _mutant(tmp_path, name)
     if name.startswith("edt_"):
         assert _edt_pins_fail(lib), f"mutation {name} not detected"
+    elif name.startswith("skiz_"):
+        assert _skiz_pins_fail(lib), f"mutation {name} not detected"
     elif name.startswith("ws_"):
         assert _ws_pins_fail(lib), f"mutation {name} not detected"
     elif name.startswith("exact_"):
