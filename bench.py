@@ -534,6 +534,53 @@ def bench_geodesic(ctx, dev, side, reps=3):
     return res
 
 
+def bench_skiz(ctx, dev, side, reps=3, cpu_sample=2048):
+    """Influence zones and SKIZ (iwpp_skiz) on the shortest-path section's
+    field: side x side with 30 % random obstacles and 256 random sources,
+    labelled 1..256.  Per-call CUDA-event times (median) of the whole call
+    (distances, then both label propagations in one launch); the oracle is
+    timed on a cpu_sample^2 crop, one thread."""
+    import statistics
+    import time
+
+    import numpy as np
+    import torch
+
+    import oracle
+
+    rng = np.random.default_rng(5000)
+    m = (rng.random((side, side), dtype=np.float32) >= 0.3).astype(np.uint8)
+    lab = np.zeros((side, side), np.int32)
+    lab[rng.integers(0, side, 256), rng.integers(0, side, 256)] = np.arange(1, 257, dtype=np.int32)
+    dm, dl = torch.from_numpy(m).to(dev), torch.from_numpy(lab).to(dev)
+    st = torch.cuda.current_stream(dev)
+    z, sk = ctx.skiz(dm, dl)
+    ctx.stats_reset()
+    times = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        z, sk = ctx.skiz(dm, dl)
+        b.record(st)
+        torch.cuda.synchronize(dev)
+        times.append(a.elapsed_time(b))
+    q = ctx.stats()
+    ms_ = statistics.median(times)
+    res = {"workload": f"{side}x{side}, 30 % random obstacles, 256 sources labelled 1..256, "
+                       "5-7 chamfer metric",
+           "ms": round(ms_, 3), "mpx_s": round(side * side / ms_ / 1e3, 1),
+           "zones": int(torch.unique(z).numel()) - 1, "skiz_px": int(sk.sum().item()),
+           "tiles_per_call": q["tiles_processed"] // reps}
+    del dm, dl, z, sk
+    if cpu_sample:
+        s = min(cpu_sample, side)
+        t0 = time.perf_counter()
+        oracle.skiz(np.ascontiguousarray(m[:s, :s]), np.ascontiguousarray(lab[:s, :s]))
+        t = time.perf_counter() - t0
+        res["cpu_oracle"] = {"mpx_s": round(s * s / t / 1e6, 3), "cores": 1, "sample": f"top-left {s}x{s} crop"}
+    return res
+
+
 def bench_watershed(ctx, dev, d_relief, side, reps=3, cpu_sample=2048):
     """Watershed from markers (iwpp_watershed) on the reconstruction's relief
     (16384^2 blurred noise, uint8, and the same values as int32) with one
@@ -767,6 +814,9 @@ def run_gpu(args, ws, rank, local):
     geodesic = None
     if rank == 0 and not args.skip_geodesic:
         geodesic = bench_geodesic(ctx, dev, side)
+    skiz = None
+    if rank == 0 and not args.skip_skiz:
+        skiz = bench_skiz(ctx, dev, side, cpu_sample=0 if args.no_cpu_baseline else 2048)
     watershed = None
     if rank == 0 and not args.skip_watershed:
         watershed = bench_watershed(ctx, dev, d_mask, side, cpu_sample=0 if args.no_cpu_baseline else 2048)
@@ -813,6 +863,7 @@ def run_gpu(args, ws, rank, local):
             "edt_exact": exact,
             "coverage": coverage,
             "geodesic": geodesic,
+            "skiz": skiz,
             "watershed": watershed,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_val, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
@@ -842,6 +893,7 @@ def main():
     ap.add_argument("--skip-coverage", action="store_true")
     ap.add_argument("--skip-geodesic", action="store_true")
     ap.add_argument("--skip-watershed", action="store_true")
+    ap.add_argument("--skip-skiz", action="store_true")
     ap.add_argument("--batch-images", type=int, default=512)
     ap.add_argument("--serve-rates", default="200,500,1000,2000")
     ap.add_argument("--serve-duration", type=float, default=1.0)

@@ -212,6 +212,32 @@ int iwpp_geodesic_async(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image 
                         int32_t *dist, void *stream);
 
 /*
+ * Influence zones of labelled sources inside a mask and their skeleton
+ * (SKIZ), which Section 1 names among the IWPP algorithms.  The paper gives
+ * no definition; this is the geodesic SKIZ (Lantuejoul, 1980) with the
+ * grid metric of iwpp_geodesic:
+ *   mask     IWPP_U8 image, free where != 0;
+ *   labels   IWPP_I32 image of the same shape (pitches may differ): a free
+ *            pixel with a label != 0 is a source of that label.  Labels
+ *            must lie in [INT32_MIN + 2, INT32_MAX - 1];
+ *   zones    (dense h*w int32, device) the least label among the labels
+ *            whose sources are nearest (least path cost, 8 moves at cost
+ *            5 / 7 through free pixels); 0 at obstacles and unreachable
+ *            pixels;
+ *   skiz     (optional, may be NULL: dense h*w uint8) 1 where two or more
+ *            labels are nearest (the skeleton by influence zones), else 0;
+ *   dist     (optional, may be NULL: dense h*w int32) the least path cost,
+ *            as iwpp_geodesic.
+ * Exact and unique.  Steps: the shortest-path propagation, then one launch
+ * that propagates the least label and the least negated label along the
+ * shortest-path edges.  Outputs must not overlap the inputs.  The context
+ * holds 6*h*w bytes of planes (10*h*w without dist) besides its workspace.
+ * Limits: h*w < 2^31.  Synchronous.
+ */
+int iwpp_skiz(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image *labels,
+              int32_t *zones, uint8_t *skiz, int32_t *dist, void *stream);
+
+/*
  * Watershed from markers, which Section 1 names among the IWPP algorithms,
  * as three wavefront propagations on the tile wavefront.  The paper gives
  * no definition; this is the image foresting transform with the

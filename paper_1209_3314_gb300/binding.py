@@ -90,6 +90,7 @@ SIGNATURES = {
     "iwpp_geodesic": (_i32, [_vp, ctypes.POINTER(Image), ctypes.POINTER(Image), _vp, _vp]),
     "iwpp_geodesic_async": (_i32, [_vp, ctypes.POINTER(Image), ctypes.POINTER(Image), _vp, _vp]),
     "iwpp_watershed": (_i32, [_vp, ctypes.POINTER(Image), ctypes.POINTER(Image), _vp, _vp, _vp]),
+    "iwpp_skiz": (_i32, [_vp, ctypes.POINTER(Image), ctypes.POINTER(Image), _vp, _vp, _vp, _vp]),
     "iwpp_recon_batched": (_i32, [_vp, _i32, ctypes.POINTER(Image), ctypes.POINTER(Image), _i32,
                                   ctypes.POINTER(Image), _vp]),
     "iwpp_edt_batched": (_i32, [_vp, _i32, ctypes.POINTER(Image), ctypes.POINTER(_vp),
@@ -321,6 +322,23 @@ class Context:
         self._check(self.lib.iwpp_watershed(self.h, ctypes.byref(f), ctypes.byref(m),
                                             ctypes.c_void_p(labels.data_ptr()), lv, _stream_ptr(stream)))
         return (labels, levels) if levels is not None else labels
+
+    def skiz(self, mask, labels, with_dist: bool = False, stream=None):
+        """Influence zones of labelled sources (free pixels with labels != 0;
+        mask uint8, labels int32 CUDA tensors of one shape) and their
+        skeleton.  Returns (zones int32, skiz uint8) or, with with_dist,
+        (zones, skiz, dist int32)."""
+        torch = _torch()
+        h, w = mask.shape
+        zones = torch.empty((h, w), dtype=torch.int32, device=mask.device)
+        sk = torch.empty((h, w), dtype=torch.uint8, device=mask.device)
+        dist = torch.empty((h, w), dtype=torch.int32, device=mask.device) if with_dist else None
+        m, lab = image_of(mask), image_of(labels)
+        self._check(self.lib.iwpp_skiz(self.h, ctypes.byref(m), ctypes.byref(lab),
+                                       ctypes.c_void_p(zones.data_ptr()), ctypes.c_void_p(sk.data_ptr()),
+                                       ctypes.c_void_p(dist.data_ptr()) if dist is not None else None,
+                                       _stream_ptr(stream)))
+        return (zones, sk, dist) if with_dist else (zones, sk)
 
     def recon_batched(self, markers, masks, conn: int = 8, outs=None, stream=None):
         torch = _torch()

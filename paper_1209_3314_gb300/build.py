@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libiwpp.so")
 
 SOURCES = ["iwpp_kernels.cu", "iwpp_api.cu", "iwpp_noalloc.cu", "iwpp_server.cu", "iwpp_edt_exact.cu",
-           "iwpp_watershed.cu"]
+           "iwpp_watershed.cu", "iwpp_skiz.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

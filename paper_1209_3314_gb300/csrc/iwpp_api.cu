@@ -798,6 +798,66 @@ int iwpp_watershed(iwpp_ctx *ctx, const iwpp_image *relief, const iwpp_image *ma
     return iwpp_sync(ctx, st);
 }
 
+int iwpp_skiz(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image *labels, int32_t *zones, uint8_t *skiz,
+              int32_t *dist, void *stream) {
+    if (!ctx) return IWPP_EINVAL;
+    int rc;
+    if ((rc = check_image(ctx, mask, "mask")) || (rc = check_image(ctx, labels, "labels"))) return rc;
+    if (mask->dtype != IWPP_U8 || labels->dtype != IWPP_I32)
+        return fail(ctx, IWPP_EINVAL, "skiz: mask must be uint8 and labels int32");
+    if (mask->h != labels->h || mask->w != labels->w)
+        return fail(ctx, IWPP_EINVAL, "skiz: mask and labels must have the same shape");
+    if (!zones) return fail(ctx, IWPP_EINVAL, "null output pointer");
+    if ((int64_t)mask->h * mask->w >= ((int64_t)1 << 31))
+        return fail(ctx, IWPP_EINVAL, "skiz limited to h*w < 2^31");
+    const int h = mask->h, w = mask->w;
+    iwpp_image zi{zones, h, w, w, IWPP_I32};
+    if (overlaps(&zi, mask) || overlaps(&zi, labels))
+        return fail(ctx, IWPP_EINVAL, "zones must not alias the mask or the labels");
+    if (dist) {
+        iwpp_image di{dist, h, w, w, IWPP_I32};
+        if (overlaps(&di, mask) || overlaps(&di, labels) || overlaps(&di, &zi))
+            return fail(ctx, IWPP_EINVAL, "dist must not alias the inputs or zones");
+    }
+    if (skiz) {
+        iwpp_image si{skiz, h, w, w, IWPP_U8};
+        if (overlaps(&si, mask) || overlaps(&si, labels) || overlaps(&si, &zi))
+            return fail(ctx, IWPP_EINVAL, "skiz must not alias the inputs or zones");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t n = (size_t)h * w;
+    const size_t oS = 0, oE = align_up(n, 256), oN = oE + align_up(n, 256), oD = oN + align_up(n * 4, 256);
+    if ((rc = ensure_aux(ctx, oD + (dist ? 0 : align_up(n * 4, 256)), st))) return rc;
+    char *aux = (char *)ctx->aux;
+    SkizArgs a;
+    a.mask = (const uint8_t *)mask->data;
+    a.labels = (const int32_t *)labels->data;
+    a.pmask = mask->pitch;
+    a.pl = labels->pitch;
+    a.h = h;
+    a.w = w;
+    a.seeds = (uint8_t *)(aux + oS);
+    a.E = (uint8_t *)(aux + oE);
+    a.neg = (int32_t *)(aux + oN);
+    a.dist = dist ? dist : (int32_t *)(aux + oD);
+    a.zones = zones;
+    a.skiz = skiz;
+    // 1. least path costs from the sources
+    CK(launch_skiz_prep(a, st), "skiz prep launch");
+    iwpp_image seeds{a.seeds, h, w, w, IWPP_U8};
+    std::vector<JobDesc> j1{gdt_job(mask, &seeds, a.dist)};
+    if ((rc = run(ctx, j1, st, false))) return rc;
+    // 2. least and greatest labels along the shortest-path edges, one launch
+    CK(launch_skiz_label_init(a, st), "skiz label init launch");
+    std::vector<JobDesc> j2{ws_job(OP_WS_LABEL, h, w, a.E, a.zones), ws_job(OP_WS_LABEL, h, w, a.E, a.neg)};
+    if ((rc = run(ctx, j2, st, false))) return rc;
+    CK(launch_skiz_finish(a, st), "skiz finish launch");
+    ctx->launches += 3;
+    ctx->calls -= 1;  // the two propagation launches are one call
+    return iwpp_sync(ctx, st);
+}
+
 int iwpp_edt_exact(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist, int32_t *nearest, int flags,
                    void *stream) {
     if (!ctx) return IWPP_EINVAL;

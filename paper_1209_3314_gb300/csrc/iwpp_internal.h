@@ -104,6 +104,24 @@ cudaError_t launch_ws_plateau_init(const WsArgs &a, cudaStream_t s);
 cudaError_t launch_ws_label_init(const WsArgs &a, cudaStream_t s);
 cudaError_t launch_ws_label_finish(const WsArgs &a, cudaStream_t s);
 
+// Influence zones / SKIZ, per-pixel steps (iwpp_skiz.cu).  Planes are dense
+// (pitch w).
+struct SkizArgs {
+    const uint8_t *mask;    // free where != 0, pitch `pmask`
+    const int32_t *labels;  // sources where free and != 0, pitch `pl`
+    int64_t pmask, pl;
+    int h, w;
+    uint8_t *seeds;         // labels != 0
+    int32_t *dist;          // shortest-path distances (INT_MAX: obstacle / unreached)
+    uint8_t *E;             // in-edge masks
+    int32_t *zones;         // least label (INT_MAX while none)
+    int32_t *neg;           // least negated label
+    uint8_t *skiz;          // optional
+};
+cudaError_t launch_skiz_prep(const SkizArgs &a, cudaStream_t s);
+cudaError_t launch_skiz_label_init(const SkizArgs &a, cudaStream_t s);
+cudaError_t launch_skiz_finish(const SkizArgs &a, cudaStream_t s);
+
 // Launch helpers implemented in iwpp_kernels.cu.
 int family_threads(int fam);
 int family_smem(int fam);
