@@ -86,8 +86,9 @@ typedef struct {
  * sweeps 3, queue_factor 32, spill_cap 8192, max_relaunch 1, timeout_ms
  * 10000, timing 0, revisit_sweep_min 0, edt_sweeps 2, edt_revisit_sweep_min
  * 64, revisit_sweeps -1, queue_mode 0, test_empty_slot 0, gdt_sweeps 8,
- * batch_split 1, ws_sweeps 2.  tile = 0 lets the autotuner choose.  Values are validated
- * by iwpp_set_options().  New fields are only ever appended. */
+ * batch_split 1, ws_sweeps 6, ws_revisit_sweep_min 0, gdt_revisit_sweep_min
+ * 4.  tile = 0 lets the autotuner choose.  Values are validated by
+ * iwpp_set_options().  New fields are only ever appended. */
 typedef struct {
     int32_t tile;            /* tile side in pixels: 0 (auto) or 64           */
     int32_t blocks_per_sm;   /* persistent CTAs per SM, 0 = as many as fit    */
@@ -131,7 +132,14 @@ typedef struct {
                                 (each with its smaller, faster kernel; the
                                 default); the autotuner tries both            */
     int32_t ws_sweeps;       /* watershed plateau-distance and label
-                                propagations: sweep sets per bulk visit       */
+                                propagations (also the SKIZ labels): sweep
+                                sets per bulk visit                           */
+    int32_t ws_revisit_sweep_min; /* the same propagations: a later visit
+                                runs the sweeps when more halo pixels than
+                                this can propagate inward, else only the
+                                queue                                         */
+    int32_t gdt_revisit_sweep_min; /* the same for the shortest-path
+                                propagation (also the SKIZ distances)         */
 } iwpp_options;
 
 /* Creates a context on `device`.  hbm_budget_bytes bounds the workspace the

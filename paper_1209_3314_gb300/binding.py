@@ -52,7 +52,8 @@ class Options(ctypes.Structure):
                 ("edt_revisit_sweep_min", ctypes.c_int32), ("revisit_sweeps", ctypes.c_int32),
                 ("queue_mode", ctypes.c_int32), ("test_empty_slot", ctypes.c_int32),
                 ("gdt_sweeps", ctypes.c_int32), ("batch_split", ctypes.c_int32),
-                ("ws_sweeps", ctypes.c_int32)]
+                ("ws_sweeps", ctypes.c_int32), ("ws_revisit_sweep_min", ctypes.c_int32),
+                ("gdt_revisit_sweep_min", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):

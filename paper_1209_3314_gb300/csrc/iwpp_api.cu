@@ -257,7 +257,9 @@ int prepare(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, const iwpp_options &opt, 
     ka.queue_mode = opt.queue_mode;
     ka.test_empty_slot = opt.test_empty_slot;
     ka.gdt_sweeps = opt.gdt_sweeps;
+    ka.gdt_revisit_sweep_min = opt.gdt_revisit_sweep_min;
     ka.ws_sweeps = opt.ws_sweeps;
+    ka.ws_revisit_sweep_min = opt.ws_revisit_sweep_min;
     ka.timeout_ns = (unsigned long long)opt.timeout_ms * 1000000ull;
     return IWPP_OK;
 }
@@ -648,7 +650,9 @@ int iwpp_ctx_create(iwpp_ctx **out, int device, size_t hbm_budget_bytes) {
     ctx->opt.revisit_sweeps = -1;
     ctx->opt.gdt_sweeps = 8;
     ctx->opt.batch_split = 1;
-    ctx->opt.ws_sweeps = 2;
+    ctx->opt.ws_sweeps = 6;
+    ctx->opt.ws_revisit_sweep_min = 0;
+    ctx->opt.gdt_revisit_sweep_min = 4;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&ctx->ctl, sizeof(Control)) != cudaSuccess ||
@@ -694,7 +698,8 @@ int iwpp_set_options(iwpp_ctx *ctx, const iwpp_options *o) {
         o->revisit_sweep_min < 0 || o->edt_sweeps < 0 || o->edt_sweeps > 64 || o->edt_revisit_sweep_min < 0 ||
         o->revisit_sweeps < -1 || o->revisit_sweeps > 64 || o->queue_mode < 0 || o->queue_mode > 3 ||
         o->test_empty_slot < 0 || o->test_empty_slot > 1 || o->gdt_sweeps < 0 || o->gdt_sweeps > 64 ||
-        o->batch_split < 0 || o->batch_split > 1 || o->ws_sweeps < 0 || o->ws_sweeps > 64)
+        o->batch_split < 0 || o->batch_split > 1 || o->ws_sweeps < 0 || o->ws_sweeps > 64 ||
+        o->ws_revisit_sweep_min < 0 || o->gdt_revisit_sweep_min < 0)
         return fail(ctx, IWPP_EINVAL, "option out of range");
     ctx->opt = *o;
     return IWPP_OK;

@@ -68,7 +68,9 @@ struct alignas(64) KArgs {
     int queue_mode;       // queue ablation: bit 0 per-thread atomics, bit 1 global-only
     int test_empty_slot;  // timeout-path tests: initial queue slot 0 left unfilled
     int gdt_sweeps;       // shortest paths: sweep sets per bulk visit
+    int gdt_revisit_sweep_min;  // and their later visits' sweep threshold
     int ws_sweeps;        // watershed propagations: sweep sets per bulk visit
+    int ws_revisit_sweep_min;  // and their later visits' sweep threshold
     unsigned long long timeout_ns;
 };
 

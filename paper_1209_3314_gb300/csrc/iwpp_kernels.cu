@@ -1621,7 +1621,7 @@ __device__ bool gdt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     } else {
         seeds = gdt_halo_seed<NT>(D, M, q0, off);
         __syncthreads();
-        if (hdr[H_CNT0] > ka.revisit_sweep_min) {
+        if (hdr[H_CNT0] > ka.gdt_revisit_sweep_min) {
             __syncthreads();
             if (tid == 0) { hdr[H_CNT0] = 0; hdr[H_RESCAN] = 0; }
             __syncthreads();
@@ -1876,7 +1876,7 @@ __device__ bool ws_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, u
     } else {
         seeds = ws_halo_seed<NT, PLAT>(V, E, q0, off);
         __syncthreads();
-        if (hdr[H_CNT0] > ka.revisit_sweep_min) {
+        if (hdr[H_CNT0] > ka.ws_revisit_sweep_min) {
             __syncthreads();
             if (tid == 0) { hdr[H_CNT0] = 0; hdr[H_RESCAN] = 0; }
             __syncthreads();

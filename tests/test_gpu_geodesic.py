@@ -106,7 +106,7 @@ def test_settings_do_not_change_the_result(cuda_ctx, sweeps, revisit_min, mode):
     rng = np.random.default_rng(95)
     m, s = field(rng, 520, 610, 0.3, 4)
     ref = oracle.gdt(m, s)
-    got = run(cuda_ctx, m, s, gdt_sweeps=sweeps, revisit_sweep_min=revisit_min, queue_mode=mode)
+    got = run(cuda_ctx, m, s, gdt_sweeps=sweeps, gdt_revisit_sweep_min=revisit_min, queue_mode=mode)
     np.testing.assert_array_equal(got, ref)
 
 

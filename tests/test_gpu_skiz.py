@@ -109,7 +109,8 @@ def test_degenerate(cuda_ctx):
     assert (s == 0).all() and (d == 0).all()
 
 
-@pytest.mark.parametrize("opts", [dict(ws_sweeps=0), dict(ws_sweeps=6), dict(gdt_sweeps=1),
+@pytest.mark.parametrize("opts", [dict(ws_sweeps=0), dict(ws_sweeps=2), dict(gdt_sweeps=1),
+                                  dict(ws_revisit_sweep_min=16), dict(gdt_revisit_sweep_min=0),
                                   dict(queue_mode=3), dict(spill_cap=0)])
 def test_settings(cuda_ctx, opts):
     rng = np.random.default_rng(220)

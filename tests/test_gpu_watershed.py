@@ -133,6 +133,7 @@ def test_degenerate(cuda_ctx):
 
 
 @pytest.mark.parametrize("opts", [dict(ws_sweeps=0), dict(ws_sweeps=1), dict(ws_sweeps=16),
+                                  dict(ws_revisit_sweep_min=8), dict(ws_revisit_sweep_min=10 ** 6),
                                   dict(queue_mode=1), dict(queue_mode=2), dict(queue_mode=3),
                                   dict(spill_cap=0), dict(blocks_per_sm=1)])
 def test_settings(cuda_ctx, opts):
