@@ -66,6 +66,7 @@ enum : int {
     H_FLAG = 13,  // 3x3 neighbourhood: needs a visit
     H_PUSH = 22, H_SPILL = 23, H_RESC = 24, H_SEEDS = 25, H_ROUNDS = 26,
     H_OFF = 32,   // 9 neighbour offsets of the current layout
+    H_CHG = 44,   // the visit lowered a value (watershed-family visits)
     H_PH = 48,    // 4 phase durations of the visit (ns, low 32 bits)
 };
 constexpr int HDR_BYTES = 512;  // header ints, mbarrier at byte 256, CTA counters at byte 320
@@ -1836,6 +1837,7 @@ __device__ bool ws_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, u
     pc.start();
     load_sources(ka, jd, tx, ty, hdr);
     begin_visit(hdr);
+    if (tid == 0) hdr[H_CHG] = 0;
     make_offsets<8, BI32_W>(hdr);
     // 1. stage the in-edge masks (0 outside the image: no edges) and the
     //    current values (the plane always holds valid values: the per-pixel
@@ -1866,9 +1868,14 @@ __device__ bool ws_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, u
     RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, qcap, ka.spill_cap, ka.queue_mode & 1};
     auto sweeps_then_seed = [&]() -> unsigned {
         bool changed = true;
-        for (int s = 0; s < ka.ws_sweeps && changed; ++s) changed = ws_sweep_set<PLAT>(V, E);
+        for (int s = 0; s < ka.ws_sweeps && changed; ++s) {
+            changed = ws_sweep_set<PLAT>(V, E);
+            if (changed && tid == 0) hdr[H_CHG] = 1;
+        }
         if (!changed && ka.ws_sweeps > 0) return 0u;
-        return ws_dilate_seed<NT, PLAT>(V, E, q0, off);
+        const unsigned lowered = ws_dilate_seed<NT, PLAT>(V, E, q0, off);
+        if (lowered) hdr[H_CHG] = 1;  // the pixels it queues are the ones it lowered
+        return lowered;
     };
     unsigned seeds;
     if (first) {
@@ -1899,6 +1906,17 @@ __device__ bool ws_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, u
                       ka.queue_mode & 1);
     __syncthreads();
     pc.mark(hdr, 2);
+
+    // A visit that lowered nothing (no sweep change, no relaxation, no
+    // queue update) leaves the plane as it was: the store is not needed,
+    // and neither is the border test -- every neighbour saw these values
+    // when it staged its halo, or will when it is visited.
+    if (!hdr[H_CHG] && hdr[H_PUSH] == 0) {
+        publish_tile(ka, gt, hdr);
+        finish_tile(ka, jd, gt, tx, ty, hdr);
+        pc.mark(hdr, 3);
+        return true;
+    }
 
     // 4. store the interior; 16-byte stores when the tile is whole and the
     //    plane meets TMA's alignment
