@@ -211,8 +211,11 @@ int iwpp_edt_exact(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist,
  * vertical) or 7 (diagonal): this build's choice of grid metric, the 5-7
  * chamfer weights.  dist (dense h*w int32, device) receives each pixel's
  * least path cost from any source: 0 at sources, INT32_MAX at obstacles
- * and unreachable pixels.  Exact (integer costs; the least cost is unique).
- * Limits: h*w < 2^31.  Not part of mixed job batches.
+ * and unreachable pixels.  Exact (integer costs; the least cost is unique)
+ * while every least path cost stays below 2^30: always with fewer than
+ * 153 M free pixels (a shortest path visits a pixel at most once, at cost
+ * <= 7 per step), and on open fields far beyond (at most 7*max(h, w)
+ * without obstacles).  Limits: h*w < 2^31.  Not part of mixed job batches.
  */
 int iwpp_geodesic(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image *seeds,
                   int32_t *dist, void *stream);
@@ -236,9 +239,9 @@ int iwpp_geodesic_async(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image 
  *            labels are nearest (the skeleton by influence zones), else 0;
  *   dist     (optional, may be NULL: dense h*w int32) the least path cost,
  *            as iwpp_geodesic.
- * Exact and unique.  Steps: the shortest-path propagation, then one launch
- * that propagates the least label and the least negated label along the
- * shortest-path edges.  Outputs must not overlap the inputs.  The context
+ * Exact and unique under iwpp_geodesic's bound on the path costs.  Steps:
+ * the shortest-path propagation, then one launch that propagates the least
+ * label and the least negated label along the shortest-path edges.  Outputs must not overlap the inputs.  The context
  * holds 6*h*w bytes of planes (10*h*w without dist) besides its workspace.
  * Limits: h*w < 2^31.  Synchronous.
  */
@@ -271,7 +274,7 @@ int iwpp_skiz(iwpp_ctx *ctx, const iwpp_image *mask, const iwpp_image *labels,
  * then the plateau distances and the labels by min-propagations along
  * per-pixel in-edge masks.  labels and levels must not overlap the inputs.
  * The context holds 2*h*w*size(relief) + 5*h*w bytes of planes besides
- * its workspace.  Limits: h*w <= 2^30.  Synchronous.
+ * its workspace.  Limits: h*w < 2^30.  Synchronous.
  */
 int iwpp_watershed(iwpp_ctx *ctx, const iwpp_image *relief, const iwpp_image *markers,
                    int32_t *labels, void *levels, void *stream);

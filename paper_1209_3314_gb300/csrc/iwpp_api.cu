@@ -482,8 +482,9 @@ int check_ws(iwpp_ctx *ctx, const iwpp_image *relief, const iwpp_image *markers,
     if (relief->h != markers->h || relief->w != markers->w)
         return fail(ctx, IWPP_EINVAL, "watershed: relief and markers must have the same shape");
     if (!labels) return fail(ctx, IWPP_EINVAL, "null output pointer");
-    if ((int64_t)relief->h * relief->w > ((int64_t)1 << 30))
-        return fail(ctx, IWPP_EINVAL, "watershed limited to h*w <= 2^30");
+    // plateau distances stay below h*w - 1 < WS_DINF, the not-reached value
+    if ((int64_t)relief->h * relief->w >= ((int64_t)1 << 30))
+        return fail(ctx, IWPP_EINVAL, "watershed limited to h*w < 2^30");
     iwpp_image lab{const_cast<int32_t *>(labels), relief->h, relief->w, relief->w, IWPP_I32};
     if (overlaps(&lab, relief) || overlaps(&lab, markers))
         return fail(ctx, IWPP_EINVAL, "labels must not alias the relief or the markers");

@@ -67,3 +67,16 @@ def test_apply_tissue_zeroes_the_background():
     assert (m2[~r] == 0).all() and (k2[~r] == 0).all()
     assert np.array_equal(m2[r], marker[r]) and np.array_equal(k2[r], mask[r])
 
+
+def test_grid_markers():
+    m = synth.grid_markers(130, 97, 32, 7)
+    # one marker per 32x32 cell (clipped at the image edge), labels 1..k in
+    # row-major cell order
+    cells = ((130 + 31) // 32) * ((97 + 31) // 32)
+    ys, xs = np.nonzero(m)
+    assert len(ys) == cells and m.dtype == np.int32
+    np.testing.assert_array_equal(np.sort(m[ys, xs]), np.arange(1, cells + 1))
+    for y, x in zip(ys, xs):
+        cy, cx = y // 32, x // 32
+        assert m[y, x] == cy * ((97 + 31) // 32) + cx + 1
+    np.testing.assert_array_equal(m, synth.grid_markers(130, 97, 32, 7))
