@@ -20,9 +20,10 @@
 //      where there is none); the label propagation then gives every pixel
 //      the least marker value that reaches it along optimal edges;
 //   4. label finish: INT_MAX (reached by no marker) becomes 0.
-// Every kernel here reads a pixel's 3x3 neighbourhood from global memory
-// (through L1) and writes the pixel: four pixels per thread with vector
-// loads and stores where the width allows, else one pixel per thread.
+// The init kernels read a pixel's 3x3 neighbourhood from global memory
+// (through L1) and write the pixel.  All of them handle four pixels per
+// thread with vector loads and stores where the width allows, else one
+// pixel per thread.
 #include <climits>
 #include <cstdint>
 

@@ -171,6 +171,30 @@ def _shift(x, dy, dx, fill):
 OFF8 = [(dy, dx) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if dy or dx]
 
 
+def test_separates_touching_disks(cuda_ctx):
+    """The use the paper's distance transform serves (Section 2.2): split
+    overlapping disks by a watershed of the negated distance map, from
+    markers at the distance maxima.  The relief comes from the library's
+    own distance transform; labels and levels must equal the oracle's on
+    that relief."""
+    from scipy import ndimage
+
+    b, _ = synth.disks_binary(384, 320, 6, 20, 0.3, 240)
+    sq, _ = cuda_ctx.edt(torch.from_numpy(b).to(DEV), feature_nonzero=False)
+    torch.cuda.synchronize()
+    d = sq.cpu().numpy()
+    relief = np.where(b != 0, -d, 0).astype(np.int32)
+    peaks = (b != 0) & (d == ndimage.maximum_filter(d, size=5)) & (d > 4)
+    markers, n = ndimage.label(peaks, structure=np.ones((3, 3), bool))
+    markers = markers.astype(np.int32)
+    markers[b == 0] = n + 1  # the background is one more basin
+    lab, lev = run(cuda_ctx, relief, markers)
+    elab, elev = oracle.watershed(relief, markers)
+    np.testing.assert_array_equal(lev, elev)
+    np.testing.assert_array_equal(lab, elab)
+    assert len(np.unique(lab[b != 0])) >= n // 2  # the disks are split into many regions
+
+
 @pytest.mark.slow
 def test_16384_certificates(cuda_ctx):
     """Full size, the bench's workload shape (16384^2 blurred relief, one
