@@ -134,9 +134,8 @@ bool make_map(CUtensorMap *m, const void *base, int dtype, int h, int w, int64_t
 
 void make_maps(JobDesc &d) {
     bool ok;
-    if (d.op == OP_GDT) {  // mask, sources, current result
+    if (d.op == OP_GDT) {  // mask, current result (sources are read directly)
         d.use_tma = make_map(&d.tm[0], d.a, DT_U8, d.h, d.w, d.pa) &&
-                    make_map(&d.tm[1], d.b, DT_U8, d.h, d.w, d.pb) &&
                     make_map(&d.tm[2], d.out, DT_I32, d.h, d.w, d.po);
         return;
     }

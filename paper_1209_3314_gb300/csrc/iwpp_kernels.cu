@@ -92,13 +92,12 @@ static_assert(
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 // geodesic distance: D as the int32 box layout (stride 72, cell (r, c) at
 // word r*72 + c + 3), the mask as a uint8 box (stride 96, cell (r, c) at
-// byte r*96 + c + 15), then the sources' uint8 box in a union with the
-// block queues (sized so that 7 CTAs fit an SM)
+// byte r*96 + c + 15), then the block queues: 30,080 bytes, so that 7 CTAs
+// fit an SM (the sources are read from global memory when needed)
 constexpr int QCAP_G = 1024;
 constexpr int G_D = HDR_BYTES, G_M = G_D + BI32_PAD, G_U = 25984;
-constexpr int G_BYTES = G_U + BU8_BYTES;
-static_assert(G_M + BU8_BYTES <= G_U && G_U % 128 == 0 && G_M % 128 == 0 && 2 * QCAP_G * 2 <= BU8_BYTES,
-              "geodesic layout");
+constexpr int G_BYTES = G_U + 2 * QCAP_G * 2;
+static_assert(G_M + BU8_BYTES <= G_U && G_U % 128 == 0 && G_M % 128 == 0, "geodesic layout");
 // watershed propagations: the same V / E boxes, the block queues after them
 constexpr int WS_BYTES = G_U + 2 * QCAP_G * 2;
 constexpr int FAM_SMEM[FAM_COUNT] = {RU8_BYTES, RI32_BYTES, E_BYTES,
@@ -1559,30 +1558,26 @@ __device__ bool gdt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     load_sources(ka, jd, tx, ty, hdr);
     begin_visit(hdr);
     make_offsets<8, BI32_W>(hdr);
-    // 1. stage the mask box (zero, i.e. obstacle, outside the image), the
-    //    current result's box (visited regions) and the sources' box
-    //    (unvisited regions: 0 at a free source, GD_INF elsewhere)
+    // 1. stage the mask box (zero, i.e. obstacle, outside the image) and
+    //    the current result's box (visited regions); in unvisited regions a
+    //    free pixel starts at 0 if it is a source (read from global memory:
+    //    a sources box would cost the CTA per SM that its 6 KB take),
+    //    else at GD_INF
     __syncthreads();
     const bool first = hdr[H_SRC + 4] == 0;
-    uint8_t *SB = (uint8_t *)(sm + G_U);
-    int need_s = 0, need_o = 0;
+    int need_o = 0;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        need_s |= hdr[H_SRC + k] == 0;
-        need_o |= hdr[H_SRC + k] == 1;
-    }
+    for (int k = 0; k < 9; ++k) need_o |= hdr[H_SRC + k] == 1;
     if (jd->use_tma) {
         if (tid == 0) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, BU8_BYTES * (1 + need_s) + need_o * BI32_BYTES);
+            mbar_arrive_expect_tx(bar, BU8_BYTES + need_o * BI32_BYTES);
             tma_load_2d(M, &jd->tm[0], x0 - 16, y0 - 1, bar);
-            if (need_s) tma_load_2d(SB, &jd->tm[1], x0 - 16, y0 - 1, bar);
             if (need_o) tma_load_2d(D, &jd->tm[2], x0 - 4, y0 - 1, bar);
         }
         if (!wait_boxes(bar, phase, deadline, ka.ctl)) return false;
     } else {
         stage_plain<uint8_t, BU8_W>(M, mk, jd->pa, jd->h, jd->w, x0 - 16, y0 - 1, NT);
-        if (need_s) stage_plain<uint8_t, BU8_W>(SB, sd, jd->pb, jd->h, jd->w, x0 - 16, y0 - 1, NT);
         if (need_o) stage_plain<int, BI32_W>(D, out, jd->po, jd->h, jd->w, x0 - 4, y0 - 1, NT);
         __syncthreads();
     }
@@ -1595,7 +1590,7 @@ __device__ bool gdt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
             if (src == 1) {
                 const int o = D[gcell(r, c)];
                 v = o < GD_INF ? o : GD_INF;
-            } else if (M[gmask(r, c)] && SB[gmask(r, c)]) {
+            } else if (M[gmask(r, c)] && __ldg(sd + (int64_t)gy * jd->pb + gx)) {
                 v = 0;
             }
         }
