@@ -96,7 +96,14 @@ typedef struct {
     int32_t queue_factor;    /* tile-queue slots = queue_factor * tiles (>= 1) */
     int32_t spill_cap;       /* global spill slots per CTA and buffer (>= 0)   */
     int32_t max_relaunch;    /* device-side relaunches after queue overflow    */
-    int32_t timeout_ms;      /* bound on any device-side wait                  */
+    int32_t timeout_ms;      /* bound on a device-side wait that sees no
+                                progress: a tile claim gives up after this
+                                long without any visit finishing or tile
+                                being queued anywhere; the TMA waits and the
+                                round guard of one tile visit give up this
+                                long after the visit began.  A call of any
+                                length that keeps making progress is never
+                                cut off.                                      */
     int32_t timing;          /* 1: bracket the persistent launches with CUDA
                                 events and add their duration to kernel_ns    */
     int32_t revisit_sweep_min; /* reconstruction: a later visit of a tile runs
@@ -311,6 +318,32 @@ int iwpp_run_jobs(iwpp_ctx *ctx, int n, const iwpp_job *jobs, void *stream);
 int iwpp_run_jobs_async(iwpp_ctx *ctx, int n, const iwpp_job *jobs, void *stream);
 
 /*
+ * Asynchronous jobs with tickets: the operations of Sections 2.1 and 2.2
+ * (one iwpp_job each, device images as in iwpp_run_jobs) enqueued on the
+ * context's own stream, which the first iwpp_submit creates.  That stream
+ * is a blocking stream: it runs after work enqueued earlier on the legacy
+ * default stream and before work enqueued there later, so inputs written
+ * on the default stream are ready.  Submitted jobs run in submission order
+ * and share the context's workspace: do not mix them with *_async calls of
+ * the same context on other streams unless those are synchronised.
+ *   iwpp_submit  validates and enqueues the job; returns at once with a
+ *                ticket (> 0) in *ticket.  Argument errors are returned
+ *                directly and give no ticket.
+ *   iwpp_poll    returns 1 when the job has finished (its outcome, IWPP_OK
+ *                or a negative IWPP_E* code, in *status; may be NULL) and
+ *                retires the ticket; 0 while it is pending; IWPP_EINVAL
+ *                for an unknown or retired ticket.
+ *   iwpp_wait    blocks until the job has finished, stores its outcome in
+ *                *status and retires the ticket; IWPP_EINVAL for an unknown
+ *                or retired ticket.
+ * Every submitted job is counted by iwpp_stats like any other call.  For a
+ * continuous-batching request loop over host images see iwpp_server_*.
+ */
+int iwpp_submit(iwpp_ctx *ctx, const iwpp_job *job, uint64_t *ticket);
+int iwpp_poll(iwpp_ctx *ctx, uint64_t ticket, int *status);
+int iwpp_wait(iwpp_ctx *ctx, uint64_t ticket, int *status);
+
+/*
  * Plans: a fixed batch of jobs prepared once for repeated launches -- tile
  * layout, TMA tensor maps, the device job table and the plan's own
  * workspace are set up by iwpp_plan_create (which may allocate and copy).
@@ -346,8 +379,14 @@ int iwpp_plan_destroy(iwpp_plan *plan);
  * (each with its own resident context), and keeps admitting new arrivals
  * onto free streams while earlier batches run.  Results are copied back to
  * the request's host buffers; the latency reported is submit-to-completion.
- * A request larger than the whole budget completes with IWPP_ENOMEM.
- * iwpp_server_destroy finishes every submitted request first.
+ * Admission counts, against the budget, the images of every request in
+ * flight and the device memory of every stream's context (its workspace
+ * grows to the largest batch it has run and stays resident).  A request
+ * that cannot fit even alone completes with IWPP_ENOMEM; creation fails with
+ * IWPP_ENOMEM when the contexts alone exceed the budget.  poll / wait hand a
+ * result out once: the ticket is then retired and a second poll or wait on
+ * it returns IWPP_EINVAL.  iwpp_server_destroy finishes every submitted
+ * request first.
  */
 typedef struct {
     int32_t op;             /* IWPP_OP_RECON or IWPP_OP_EDT                      */
@@ -364,13 +403,19 @@ typedef struct {
 
 typedef struct {
     uint64_t submitted, completed, batches, pending;
-    uint64_t bytes_in_use, peak_bytes_in_use;
+    uint64_t bytes_in_use;       /* request images in flight + resident workspaces */
+    uint64_t peak_bytes_in_use;  /* peak of bytes_in_use (admission keeps it <= budget) */
+    uint64_t workspace_bytes;    /* device memory the streams' contexts hold */
+    uint64_t pool_used_high;     /* high-water mark of the device's default memory
+                                    pool (request images) since server creation */
+    uint64_t records;            /* finished results not yet handed out */
 } iwpp_server_stats_t;
 
 typedef struct iwpp_server iwpp_server;
 int iwpp_server_create(iwpp_server **out, int device, size_t hbm_budget_bytes, int streams, int max_batch);
 int iwpp_server_submit(iwpp_server *srv, const iwpp_request *req, uint64_t *ticket);
-/* 1 when the request finished (its status in *status), 0 while pending. */
+/* 1 when the request finished (its status in *status; the ticket is then
+ * retired), 0 while pending, IWPP_EINVAL for an unknown or retired ticket. */
 int iwpp_server_poll(iwpp_server *srv, uint64_t ticket, int *status);
 /* Blocks until the request finished; *status is its outcome. */
 int iwpp_server_wait(iwpp_server *srv, uint64_t ticket, int *status, double *latency_ms);
@@ -385,14 +430,16 @@ int iwpp_stats(iwpp_ctx *ctx, iwpp_stats_t *out);
 int iwpp_stats_reset(iwpp_ctx *ctx);
 
 /*
- * Allocation-free uint8 reconstruction (the paper has no counterpart; it
- * exists for callers that cannot allocate device memory: code inside
- * another allocator's accounting, real-time paths that forbid allocation
- * after start-up, and code being recorded into a CUDA graph).
+ * Allocation-free uint8 reconstruction.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory --
+ * code running inside another allocator's accounting (a caching allocator
+ * that owns the device budget) and real-time paths that forbid allocation
+ * after start-up (cudaMalloc may block and synchronise the device).
  *
  * Same operation and result as iwpp_recon on IWPP_U8 images, without a
  * context: marker, mask and out are device pointers with pitches in bytes;
- * out may be marker (in place) but not mask; conn = 4 or 8; the work is
+ * out may be marker exactly (in place, equal pitches) but must not overlap
+ * the mask or partly overlap the marker; conn = 4 or 8; the work is
  * enqueued on `stream` and the call returns after it finished.  All
  * scratch (tile queue, tile states, spill queues, status block) lives in one
  * statically sized device array of IWPP_NOALLOC_SCRATCH_BYTES held by every
@@ -400,10 +447,13 @@ int iwpp_stats_reset(iwpp_ctx *ctx);
  * nothing.  Limits and rules:
  *   - at most IWPP_NOALLOC_MAX_TILES tiles of 64x64 pixels (e.g. 16384 x
  *     16384); larger images return IWPP_EINVAL;
- *   - all calls share the array: calls whose GPU work overlaps (different
- *     streams or threads on one device) race -- serialise them;
+ *   - all calls share the array, which keeps the last call's contents (each
+ *     call clears its status block and refills its queue before it runs):
+ *     calls whose GPU work overlaps (different streams or threads on one
+ *     device) race -- serialise them;
  *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make it before any stream capture.
+ *     (cudaGetSymbolAddress); make it before any stream capture;
+ *   - a device-side wait gives up after 10 s without progress.
  * Returns IWPP_OK, IWPP_EINVAL, IWPP_ECUDA, IWPP_ETIMEOUT or IWPP_EOVERFLOW.
  */
 #define IWPP_NOALLOC_MAX_TILES 65536

@@ -65,7 +65,8 @@ class Request(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "batches", "pending",
-                                                 "bytes_in_use", "peak_bytes_in_use")]
+                                                 "bytes_in_use", "peak_bytes_in_use", "workspace_bytes",
+                                                 "pool_used_high", "records")]
 
 
 class Job(ctypes.Structure):
@@ -98,6 +99,9 @@ SIGNATURES = {
                                 ctypes.POINTER(_vp), _i32, _vp]),
     "iwpp_run_jobs": (_i32, [_vp, _i32, ctypes.POINTER(Job), _vp]),
     "iwpp_run_jobs_async": (_i32, [_vp, _i32, ctypes.POINTER(Job), _vp]),
+    "iwpp_submit": (_i32, [_vp, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]),
+    "iwpp_poll": (_i32, [_vp, ctypes.c_uint64, ctypes.POINTER(_i32)]),
+    "iwpp_wait": (_i32, [_vp, ctypes.c_uint64, ctypes.POINTER(_i32)]),
     "iwpp_sync": (_i32, [_vp, _vp]),
     "iwpp_stats": (_i32, [_vp, ctypes.POINTER(Stats)]),
     "iwpp_stats_reset": (_i32, [_vp]),
@@ -377,6 +381,37 @@ class Context:
         arr = _job_array(jobs)
         fn = self.lib.iwpp_run_jobs if sync else self.lib.iwpp_run_jobs_async
         self._check(fn(self.h, n, arr, _stream_ptr(stream)))
+
+
+    # ---- asynchronous jobs with tickets (the context's own stream)
+    def submit(self, job) -> int:
+        """Enqueues one job (a dict as for ``run_jobs``) on the context's own
+        stream and returns its ticket at once.  The job's tensors are kept
+        alive until the ticket is retired by ``poll`` or ``wait``."""
+        arr = _job_array([job])
+        t = ctypes.c_uint64(0)
+        self._check(self.lib.iwpp_submit(self.h, arr, ctypes.byref(t)))
+        self.__dict__.setdefault("_submitted", {})[t.value] = job
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while the job runs; its outcome code (0 = IWPP_OK) once it
+        has finished (the ticket is then retired)."""
+        st = ctypes.c_int(0)
+        rc = self.lib.iwpp_poll(self.h, ticket, ctypes.byref(st))
+        if rc < 0:
+            self._check(rc)
+        if rc == 0:
+            return None
+        self.__dict__.get("_submitted", {}).pop(ticket, None)
+        return st.value
+
+    def wait(self, ticket: int) -> int:
+        """Blocks until the job has finished; returns its outcome code."""
+        st = ctypes.c_int(0)
+        self._check(self.lib.iwpp_wait(self.h, ticket, ctypes.byref(st)))
+        self.__dict__.get("_submitted", {}).pop(ticket, None)
+        return st.value
 
 
 def _job_array(jobs):

@@ -33,6 +33,19 @@ struct iwpp_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending_events, free_events;
     int occupancy[FAM_COUNT] = {};  // blocks per SM per kernel family
     std::map<uint64_t, iwpp_options> tuned;   // autotuner results by workload key
+    // submitted jobs (iwpp_submit): the context's own stream, a ring of
+    // pinned status words (one per outstanding ticket) and the completion
+    // event of every ticket not yet retired by iwpp_poll / iwpp_wait
+    struct Ticket {
+        cudaEvent_t ev = nullptr;
+        int slot = -1;      // ring slot of its status word, -1 once moved to `status`
+        int status = 0;     // ST_* bits, valid once slot == -1
+    };
+    cudaStream_t sub_stream = nullptr;
+    int *h_sub_status = nullptr;              // kSubRing pinned ints
+    std::vector<uint64_t> sub_slot_owner;     // ticket holding each ring slot (0 = free)
+    std::map<uint64_t, Ticket> tickets;
+    uint64_t next_ticket = 1;
 };
 
 namespace {
@@ -154,6 +167,7 @@ void make_maps(JobDesc &d) {
 }
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+size_t ws_alloc_size(const iwpp_ctx *ctx, size_t bytes);
 
 int ensure_ws(iwpp_ctx *ctx, size_t bytes, cudaStream_t st) {
     if (bytes <= ctx->ws_bytes) return IWPP_OK;
@@ -165,8 +179,7 @@ int ensure_ws(iwpp_ctx *ctx, size_t bytes, cudaStream_t st) {
         ctx->ws = nullptr;
         ctx->ws_bytes = 0;
     }
-    size_t b = align_up(bytes + bytes / 4, 1 << 20);
-    if (ctx->budget && b > ctx->budget) b = bytes;
+    const size_t b = ws_alloc_size(ctx, bytes);
     cudaError_t e = cudaMalloc(&ctx->ws, b);
     if (e != cudaSuccess) {
         ctx->ws = nullptr;
@@ -216,6 +229,43 @@ struct Prepared {
     size_t o_slots = 0, o_state = 0, o_visited = 0, o_cnt = 0, o_spill = 0, o_jobs = 0;
 };
 
+// Byte offsets of a launch's workspace: tile-queue slots, tile states and
+// visited flags, queue counters, per-CTA spill queues, the job table.
+void layout_workspace(Prepared &P, int64_t cap64, size_t njobs, const iwpp_options &opt) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    P.o_slots = take((size_t)cap64 * 4);
+    P.o_state = take((size_t)P.ntiles * 4);
+    P.o_visited = take((size_t)P.ntiles * 4);
+    P.o_cnt = take(16);
+    P.o_spill = take((size_t)P.grid * 2 * std::max(1, opt.spill_cap) * sizeof(uint16_t));
+    P.o_jobs = take(njobs > 1 ? njobs * sizeof(JobDesc) : 0);
+    P.ws_bytes = off;
+}
+
+// The workspace bytes a launch sequence over `jobs` needs (no TMA encoding,
+// no allocation): the same arithmetic as prepare().
+int workspace_need(iwpp_ctx *ctx, std::vector<JobDesc> jobs, const iwpp_options &opt, size_t *bytes) {
+    Prepared P;
+    P.fam = pick_family(jobs);
+    P.ntiles = layout_jobs(jobs, TILE);
+    const int64_t cap64 = std::max<int64_t>(P.ntiles + 1, (int64_t)opt.queue_factor * P.ntiles);
+    int &occ = ctx->occupancy[P.fam];
+    if (occ == 0) CK(family_occupancy(P.fam, &occ), "occupancy query");
+    const int bps = opt.blocks_per_sm > 0 ? std::min(opt.blocks_per_sm, occ) : occ;
+    P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(P.ntiles, (int64_t)bps * ctx->sm_count));
+    layout_workspace(P, cap64, jobs.size(), opt);
+    *bytes = P.ws_bytes;
+    return IWPP_OK;
+}
+
+// The size ensure_ws() allocates for a request of `bytes`.
+size_t ws_alloc_size(const iwpp_ctx *ctx, size_t bytes) {
+    size_t b = align_up(bytes + bytes / 4, 1 << 20);
+    if (ctx->budget && b > ctx->budget) b = bytes;
+    return b;
+}
+
 int prepare(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, const iwpp_options &opt, Prepared &P) {
     P.fam = pick_family(jobs);
     P.ntiles = layout_jobs(jobs, TILE);
@@ -231,15 +281,7 @@ int prepare(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, const iwpp_options &opt, 
     }
     const int bps = opt.blocks_per_sm > 0 ? std::min(opt.blocks_per_sm, occ) : occ;
     P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(P.ntiles, (int64_t)bps * ctx->sm_count));
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-    P.o_slots = take((size_t)cap64 * 4);
-    P.o_state = take((size_t)P.ntiles * 4);
-    P.o_visited = take((size_t)P.ntiles * 4);
-    P.o_cnt = take(16);
-    P.o_spill = take((size_t)P.grid * 2 * std::max(1, opt.spill_cap) * sizeof(uint16_t));
-    P.o_jobs = take(jobs.size() > 1 ? jobs.size() * sizeof(JobDesc) : 0);
-    P.ws_bytes = off;
+    layout_workspace(P, cap64, jobs.size(), opt);
     KArgs &ka = P.ka;
     memset(&ka, 0, sizeof ka);
     ka.njobs = (int)jobs.size();
@@ -671,6 +713,13 @@ int iwpp_ctx_create(iwpp_ctx **out, int device, size_t hbm_budget_bytes) {
 int iwpp_ctx_destroy(iwpp_ctx *ctx) {
     if (!ctx) return IWPP_OK;
     cudaSetDevice(ctx->device);
+    if (ctx->sub_stream) {
+        cudaStreamSynchronize(ctx->sub_stream);
+        cudaStreamDestroy(ctx->sub_stream);
+    }
+    for (auto &t : ctx->tickets)
+        if (t.second.ev) cudaEventDestroy(t.second.ev);
+    if (ctx->h_sub_status) cudaFreeHost(ctx->h_sub_status);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->aux) cudaFree(ctx->aux);
     if (ctx->ctl) cudaFree(ctx->ctl);
@@ -967,6 +1016,168 @@ int iwpp_run_jobs_async(iwpp_ctx *ctx, int n, const iwpp_job *js, void *stream) 
     if (rc) return rc;
     return run(ctx, jobs, (cudaStream_t)stream, false);
 }
+
+}  // extern "C"
+
+namespace {
+
+constexpr int kSubRing = 256;  // outstanding tickets with a status word in the ring
+
+int status_code(iwpp_ctx *ctx, int errors) {
+    if (errors & ST_TIMEOUT) return fail(ctx, IWPP_ETIMEOUT, "a device-side wait saw no progress for %d ms",
+                                         ctx->opt.timeout_ms);
+    if (errors & ST_OVERFLOW) return fail(ctx, IWPP_EOVERFLOW, "tile queue overflowed after %d relaunches",
+                                          ctx->opt.max_relaunch);
+    return IWPP_OK;
+}
+
+// Waits for ticket t's event and keeps its status word on the host, so
+// that its ring slot can serve another ticket.
+int settle_ticket(iwpp_ctx *ctx, iwpp_ctx::Ticket &t) {
+    if (t.slot < 0) return IWPP_OK;
+    CK(cudaEventSynchronize(t.ev), "cudaEventSynchronize");
+    t.status = ctx->h_sub_status[t.slot];
+    ctx->sub_slot_owner[t.slot] = 0;
+    t.slot = -1;
+    return IWPP_OK;
+}
+
+// A free ring slot; when all are held, the oldest outstanding ticket is
+// settled first.
+int take_slot(iwpp_ctx *ctx, int *slot) {
+    for (int i = 0; i < kSubRing; ++i)
+        if (ctx->sub_slot_owner[i] == 0) {
+            *slot = i;
+            return IWPP_OK;
+        }
+    for (auto &kv : ctx->tickets)
+        if (kv.second.slot >= 0) {
+            const int s = kv.second.slot;
+            int rc = settle_ticket(ctx, kv.second);
+            if (rc) return rc;
+            *slot = s;
+            return IWPP_OK;
+        }
+    return fail(ctx, IWPP_ECUDA, "submit: no status slot");
+}
+
+int retire(iwpp_ctx *ctx, uint64_t ticket, int *status) {
+    auto it = ctx->tickets.find(ticket);
+    iwpp_ctx::Ticket t = it->second;
+    ctx->tickets.erase(it);
+    if (t.ev) cudaEventDestroy(t.ev);
+    const int rc = status_code(ctx, t.status);
+    if (status) *status = rc;
+    return IWPP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int iwpp_submit(iwpp_ctx *ctx, const iwpp_job *job, uint64_t *ticket) {
+    if (!ctx) return IWPP_EINVAL;
+    if (!job || !ticket) return fail(ctx, IWPP_EINVAL, "submit: job and ticket required");
+    *ticket = 0;
+    std::vector<JobDesc> jobs;
+    int rc = jobs_from(ctx, 1, job, jobs);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (!ctx->sub_stream) {
+        // a blocking stream: ordered with work on the legacy default stream
+        CK(cudaStreamCreate(&ctx->sub_stream), "cudaStreamCreate");
+        CK(cudaMallocHost(&ctx->h_sub_status, kSubRing * sizeof(int)), "cudaMallocHost");
+        ctx->sub_slot_owner.assign(kSubRing, 0);
+    }
+    int slot = -1;
+    if ((rc = take_slot(ctx, &slot))) return rc;
+    cudaStream_t st = ctx->sub_stream;
+    if ((rc = run(ctx, jobs, st, false))) return rc;
+    // the job's outcome word goes to its own status slot, then the shared
+    // word is cleared for the next job on the stream
+    CK(cudaMemcpyAsync(ctx->h_sub_status + slot, &ctx->ctl->errors, sizeof(int), cudaMemcpyDeviceToHost, st),
+       "status readback");
+    CK(cudaMemsetAsync(&ctx->ctl->errors, 0, sizeof(int), st), "status reset");
+    iwpp_ctx::Ticket t;
+    CK(cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming), "cudaEventCreate");
+    cudaError_t e = cudaEventRecord(t.ev, st);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(t.ev);
+        return cuda_fail(ctx, e, "cudaEventRecord");
+    }
+    t.slot = slot;
+    const uint64_t id = ctx->next_ticket++;
+    ctx->sub_slot_owner[slot] = id;
+    ctx->tickets[id] = t;
+    *ticket = id;
+    return IWPP_OK;
+}
+
+int iwpp_poll(iwpp_ctx *ctx, uint64_t ticket, int *status) {
+    if (!ctx) return IWPP_EINVAL;
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(ctx, IWPP_EINVAL, "poll: unknown or retired ticket %llu",
+                                              (unsigned long long)ticket);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    iwpp_ctx::Ticket &t = it->second;
+    if (t.slot >= 0) {
+        const cudaError_t e = cudaEventQuery(t.ev);
+        if (e == cudaErrorNotReady) {
+            (void)cudaGetLastError();
+            return 0;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventQuery");
+        int rc = settle_ticket(ctx, t);
+        if (rc) return rc;
+    }
+    int rc = retire(ctx, ticket, status);
+    return rc ? rc : 1;
+}
+
+int iwpp_wait(iwpp_ctx *ctx, uint64_t ticket, int *status) {
+    if (!ctx) return IWPP_EINVAL;
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(ctx, IWPP_EINVAL, "wait: unknown or retired ticket %llu",
+                                              (unsigned long long)ticket);
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int rc = settle_ticket(ctx, it->second);
+    if (rc) return rc;
+    return retire(ctx, ticket, status);
+}
+
+}  // extern "C"
+
+namespace iwpp {
+
+size_t ctx_device_bytes(const iwpp_ctx *ctx) {
+    return ctx->ws_bytes + ctx->aux_bytes + sizeof(Control);
+}
+
+int ctx_device_bytes_after(iwpp_ctx *ctx, int n, const int *op, const int *dtype, const int *h, const int *w,
+                           size_t *bytes) {
+    std::vector<JobDesc> jobs(n);
+    for (int i = 0; i < n; ++i) {
+        memset(&jobs[i], 0, sizeof(JobDesc));
+        jobs[i].op = op[i] == IWPP_OP_RECON ? OP_RECON : OP_EDT;
+        jobs[i].dtype = dtype[i] == IWPP_I32 ? DT_I32 : DT_U8;
+        jobs[i].h = h[i];
+        jobs[i].w = w[i];
+    }
+    size_t need = 0;
+    int rc;
+    for (const std::vector<JobDesc> &g : launch_groups(jobs, ctx->opt.batch_split)) {
+        size_t b = 0;
+        if ((rc = workspace_need(ctx, g, ctx->opt, &b))) return rc;
+        need += align_up(b, 256);
+    }
+    const size_t ws = need <= ctx->ws_bytes ? ctx->ws_bytes : ws_alloc_size(ctx, need);
+    *bytes = ws + ctx->aux_bytes + sizeof(Control);
+    return IWPP_OK;
+}
+
+}  // namespace iwpp
+
+extern "C" {
 
 int iwpp_sync(iwpp_ctx *ctx, void *stream) {
     if (!ctx) return IWPP_EINVAL;

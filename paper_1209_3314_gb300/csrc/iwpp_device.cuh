@@ -94,13 +94,17 @@ __device__ __forceinline__ void st_release(int *p, int v) {
 
 // Claims the next tile (called by ONE thread).  Returns the tile id, or -1
 // when the whole launch is finished (nothing queued or in process), the
-// ticket lies beyond the queue capacity, or the deadline passed (then
-// ST_TIMEOUT is raised).
-__device__ inline int tq_claim(const TileQueue &q, Control *ctl,
-                               unsigned long long deadline) {
+// ticket lies beyond the queue capacity, or the wait saw no progress for
+// `timeout_ns` (then ST_TIMEOUT is raised).  The bound is on a wait without
+// progress, not on the work: while other CTAs finish visits or queue tiles
+// (the pending count or the reservation counter moves), the wait goes on.
+__device__ inline int tq_claim(const TileQueue &q, Control *ctl, unsigned long long timeout_ns) {
     unsigned int h = atomicAdd(q.head, 1u);
     if (h >= q.cap) return -1;
     unsigned int ns = 32;
+    unsigned long long last = globaltimer_ns();
+    int seen_pending = ld_volatile(q.pending);
+    unsigned int seen_tail = *(volatile unsigned int *)q.tail;
     while (true) {
         int t = ld_acquire(q.slots + h);
         if (t >= 0) {
@@ -108,8 +112,15 @@ __device__ inline int tq_claim(const TileQueue &q, Control *ctl,
             __threadfence();
             return t;
         }
-        if (ld_volatile(q.pending) == 0) return -1;
-        if (globaltimer_ns() > deadline) {
+        const int pend = ld_volatile(q.pending);
+        if (pend == 0) return -1;
+        const unsigned int tail = *(volatile unsigned int *)q.tail;
+        const unsigned long long now = globaltimer_ns();
+        if (pend != seen_pending || tail != seen_tail) {
+            seen_pending = pend;
+            seen_tail = tail;
+            last = now;
+        } else if (now - last > timeout_ns) {
             atomicOr(&ctl->status, ST_TIMEOUT);
             atomicOr(&ctl->sticky, ST_TIMEOUT);
             return -1;

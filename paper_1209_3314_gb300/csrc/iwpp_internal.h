@@ -124,6 +124,21 @@ cudaError_t launch_skiz_prep(const SkizArgs &a, cudaStream_t s);
 cudaError_t launch_skiz_label_init(const SkizArgs &a, cudaStream_t s);
 cudaError_t launch_skiz_finish(const SkizArgs &a, cudaStream_t s);
 
+}  // namespace iwpp
+
+struct iwpp_ctx;
+
+namespace iwpp {
+
+// Device memory a context holds (workspace, planes, control block), now and
+// after it has run one batch of n reconstruction / distance-transform jobs
+// of the given ops (IWPP_OP_*), dtypes (IWPP_U8 / IWPP_I32) and shapes --
+// which may grow its workspace (iwpp_api.cu; the server's admission counts
+// it).
+size_t ctx_device_bytes(const iwpp_ctx *ctx);
+int ctx_device_bytes_after(iwpp_ctx *ctx, int n, const int *op, const int *dtype, const int *h, const int *w,
+                           size_t *bytes);
+
 // Launch helpers implemented in iwpp_kernels.cu.
 int family_threads(int fam);
 int family_smem(int fam);

@@ -1974,13 +1974,12 @@ __global__ void __launch_bounds__(FAM_NT[FAM], FAM_MINB[FAM]) persistent_kernel(
     if (threadIdx.x < 10) cst[threadIdx.x] = 0;
     __syncthreads();
     uint32_t phase = 0;
-    const unsigned long long deadline = globaltimer_ns() + ka.timeout_ns;
     unsigned long long t_wait = 0, t_visit = 0;
     while (true) {
         unsigned long long t0 = 0;
         if (threadIdx.x == 0) {
             t0 = globaltimer_ns();
-            hdr[H_TILE] = tq_claim(ka.tq, ka.ctl, deadline);
+            hdr[H_TILE] = tq_claim(ka.tq, ka.ctl, ka.timeout_ns);
             const unsigned long long t1 = globaltimer_ns();
             t_wait += t1 - t0;
             t0 = t1;
@@ -1988,6 +1987,11 @@ __global__ void __launch_bounds__(FAM_NT[FAM], FAM_MINB[FAM]) persistent_kernel(
         __syncthreads();
         const int t = hdr[H_TILE];
         if (t < 0) break;
+        // waits inside one visit (its TMA boxes, the guard of its rounds) are
+        // bounded from the visit's start: a visit takes micro- to
+        // milliseconds, so only a defect reaches the bound; a long call made
+        // of many visits does not
+        const unsigned long long deadline = globaltimer_ns() + ka.timeout_ns;
         const JobDesc *jd = job_of(ka, t);
         bool ok = true;
         if (jd->op == OP_RECON) {

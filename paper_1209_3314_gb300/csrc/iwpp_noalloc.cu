@@ -3,25 +3,29 @@
 //
 // Some callers must not call cudaMalloc: code running inside another
 // allocator's or a framework's memory accounting (a caching allocator that
-// owns the whole device budget), real-time paths that forbid allocation
-// after start-up, and code paths being recorded into a CUDA graph, where a
-// cudaMalloc would be illegal.  The regular entry points take their
-// workspace (tile queue, tile states, spill queues, status block) from a
-// context, and creating or growing a context allocates.  This entry point
-// instead uses one statically sized scratch array compiled into the
-// library (file scope, __device__), so it needs no context and performs no
-// allocation of its own.
+// owns the whole device budget, where a side allocation would go unseen or
+// fail), and real-time paths that forbid allocation after start-up because
+// cudaMalloc can block and synchronise the device.  The regular entry
+// points take their workspace (tile queue, tile states, spill queues,
+// status block) from a context, and creating or growing a context
+// allocates.  This entry point instead uses one statically sized scratch
+// array compiled into the library (file scope, __device__), so it needs no
+// context and performs no allocation of its own.
 //
 // Properties a caller must know:
 //   * the scratch array (IWPP_NOALLOC_SCRATCH_BYTES) occupies device memory
 //     on every GPU that loads the library, from load until process exit;
-//   * every call uses the same array: two calls whose GPU work overlaps
-//     (different streams, or different host threads on one device) race
-//     and corrupt each other's results -- order them on one stream;
+//   * every call uses the same array and it keeps the last call's contents
+//     (each call clears its status block and refills its queue first): two
+//     calls whose GPU work overlaps (different streams, or different host
+//     threads on one device) race and corrupt each other's results -- order
+//     them on one stream;
 //   * the first call on a device resolves the array's device address with
 //     cudaGetSymbolAddress; make that first call before any stream capture;
 //   * images larger than the array supports are rejected with IWPP_EINVAL
-//     (no more than IWPP_NOALLOC_MAX_TILES tiles of 64x64 pixels).
+//     (no more than IWPP_NOALLOC_MAX_TILES tiles of 64x64 pixels);
+//   * the call is synchronous: it returns after the work on `stream` has
+//     finished and its outcome word has been read back.
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -91,9 +95,13 @@ extern "C" int iwpp_recon_u8_noalloc(const uint8_t *marker, int64_t marker_pitch
     if (marker_pitch < w || mask_pitch < w || out_pitch < w) return IWPP_EINVAL;
     const int64_t tiles_x = (w + TILE - 1) / TILE, tiles_y = (h + TILE - 1) / TILE;
     if (tiles_x * tiles_y > kMaxTiles) return IWPP_EINVAL;  // beyond the scratch array
-    if (out == mask) return IWPP_EINVAL;
-    if (out != marker && out < marker + (int64_t)(h - 1) * marker_pitch + w && marker < out + (int64_t)(h - 1) * out_pitch + w)
-        return IWPP_EINVAL;
+    // byte ranges [first, last) of the three images: out may be the marker
+    // exactly (in place) but must not touch the mask at all
+    const uint8_t *out_end = out + (int64_t)(h - 1) * out_pitch + w;
+    const uint8_t *mask_end = mask + (int64_t)(h - 1) * mask_pitch + w;
+    const uint8_t *marker_end = marker + (int64_t)(h - 1) * marker_pitch + w;
+    if (out < mask_end && mask < out_end) return IWPP_EINVAL;
+    if (out != marker && out < marker_end && marker < out_end) return IWPP_EINVAL;
     if (out == marker && out_pitch != marker_pitch) return IWPP_EINVAL;
 
     int dev = 0;
@@ -145,6 +153,8 @@ extern "C" int iwpp_recon_u8_noalloc(const uint8_t *marker, int64_t marker_pitch
     ka.sweeps = 3;
     ka.revisit_sweeps = 3;
     ka.revisit_sweep_min = 0;
+    // a device-side wait gives up after 10 s without progress (a long call
+    // that keeps making progress is not cut off)
     ka.timeout_ns = 10000000000ull;
     int grid = slot->occupancy * slot->sm_count;
     if (grid > kMaxGrid) grid = kMaxGrid;

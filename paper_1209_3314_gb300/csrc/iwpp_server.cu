@@ -2,10 +2,12 @@
 //
 // Requests (a reconstruction or a distance transform on host images) are
 // queued by iwpp_server_submit and served by one worker thread:
-//   * admission: a request is admitted when the device memory its images
-//     need fits the server's HBM budget next to everything in flight
-//     (stream-ordered allocations from the device's memory pool, which
-//     keeps freed blocks cached for the next requests);
+//   * admission: a request is admitted when the device memory it needs
+//     fits the server's HBM budget next to everything else the server holds:
+//     the images of the requests in flight (stream-ordered allocations from
+//     the device's memory pool, which keeps freed blocks cached for the next
+//     requests) and the resident workspace of every stream's context, grown
+//     to what the batch needs (tile queue, tile states, spill queues);
 //   * batching: the admitted requests form one batch, run as ONE persistent
 //     launch (iwpp_run_jobs_async) on one of the server's streams; each
 //     stream has its own resident context (tile queue, flags, spill space);
@@ -15,7 +17,9 @@
 //   * completion: host-to-device copies, the launch and device-to-host
 //     copies are ordered on the batch's stream; an event marks the end.
 //     The worker polls the events, releases the memory, and records each
-//     request's status and latency (submit to completion).
+//     request's status and latency (submit to completion), which
+//     iwpp_server_poll / iwpp_server_wait hand out once (then the ticket is
+//     retired and its record dropped).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -23,10 +27,12 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <vector>
 
 #include "../../include/iwpp.h"
+#include "iwpp_internal.h"
 
 namespace {
 
@@ -51,15 +57,19 @@ struct Slot {  // one stream with its resident context
     bool busy = false;
     std::vector<Request> batch;
     std::vector<void *> allocs;
-    size_t bytes = 0;
+    size_t bytes = 0;      // request images of the batch in flight
+    size_t ctx_bytes = 0;  // device memory the slot's context holds (resident)
 };
 
 size_t elem(int dtype) { return dtype == IWPP_I32 ? 4 : 1; }
 
+// Device bytes of a request's three buffers, each rounded up to 2 MiB so that
+// the count never falls below what the memory pool hands out for them.
 size_t request_bytes(const iwpp_request &r) {
     const size_t px = (size_t)r.h * r.w;
-    if (r.op == IWPP_OP_RECON) return 3 * px * elem(r.dtype) + 3 * 256;
-    return px + 8 * px + 3 * 256;
+    auto round = [](size_t n) { return (n + ((size_t)2 << 20) - 1) / ((size_t)2 << 20) * ((size_t)2 << 20); };
+    if (r.op == IWPP_OP_RECON) return 3 * round(px * elem(r.dtype));
+    return round(px) + 2 * round(4 * px);
 }
 
 }  // namespace
@@ -72,9 +82,13 @@ struct iwpp_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request> pending;
-    std::map<uint64_t, Done> done;
+    std::map<uint64_t, Done> done;  // finished, not yet handed out
+    std::set<uint64_t> live;        // submitted, not yet handed out
     uint64_t next_ticket = 1;
-    size_t in_use = 0, peak_in_use = 0;
+    size_t in_use = 0;              // request images in flight
+    size_t ws_total = 0;            // resident context memory of all slots
+    size_t peak_in_use = 0;         // peak of in_use + ws_total
+    cudaMemPool_t pool = nullptr;
     uint64_t batches = 0, completed = 0, submitted = 0;
     bool stop = false;
     std::thread worker;
@@ -172,29 +186,58 @@ void iwpp_server::run() {
         for (Slot &s : slots) {
             if (s.busy || pending.empty()) continue;
             std::vector<Request> batch;
-            size_t bytes = 0;
+            std::vector<int> op, dt, hh, ww;
+            size_t bytes = 0, ctx_after = s.ctx_bytes;
+            const size_t others_ws = ws_total - s.ctx_bytes;
             while (!pending.empty() && (int)batch.size() < max_batch) {
                 const Request &r = pending.front();
-                if (r.bytes > budget) {  // can never fit: fail it
-                    done[r.ticket] = Done{IWPP_ENOMEM, 0.0};
+                // the slot context's memory once it has run the batch with r
+                op.push_back(r.req.op);
+                dt.push_back(r.req.op == IWPP_OP_RECON ? r.req.dtype : IWPP_U8);
+                hh.push_back(r.req.h);
+                ww.push_back(r.req.w);
+                size_t after = 0, alone = 0;
+                const bool sized =
+                    iwpp::ctx_device_bytes_after(s.ctx, (int)op.size(), op.data(), dt.data(), hh.data(), ww.data(),
+                                                 &after) == IWPP_OK &&
+                    iwpp::ctx_device_bytes_after(s.ctx, 1, &op.back(), &dt.back(), &hh.back(), &ww.back(),
+                                                 &alone) == IWPP_OK;
+                if (!sized || others_ws + alone + r.bytes > budget) {
+                    // can never fit, even alone on this stream: fail it
+                    done[r.ticket] = Done{sized ? IWPP_ENOMEM : IWPP_ECUDA, 0.0};
                     ++completed;
                     pending.pop_front();
+                    op.pop_back(); dt.pop_back(); hh.pop_back(); ww.pop_back();
                     cv_done.notify_all();
                     continue;
                 }
-                if (in_use + bytes + r.bytes > budget) break;
+                if (in_use + bytes + r.bytes + others_ws + after > budget) {
+                    op.pop_back(); dt.pop_back(); hh.pop_back(); ww.pop_back();
+                    break;
+                }
                 bytes += r.bytes;
+                ctx_after = after;
                 batch.push_back(r);
                 pending.pop_front();
             }
             if (batch.empty()) break;  // memory exhausted: wait for completions
             in_use += bytes;
-            peak_in_use = std::max(peak_in_use, in_use);
+            ws_total += ctx_after - s.ctx_bytes;  // reserved before the context grows
+            s.ctx_bytes = ctx_after;
+            peak_in_use = std::max(peak_in_use, in_use + ws_total);
             ++batches;
             s.bytes = bytes;
             lock.unlock();
             const bool ok = launch(s, std::move(batch));
             lock.lock();
+            {   // what the context really holds now (never more than reserved)
+                const size_t real = iwpp::ctx_device_bytes(s.ctx);
+                if (real > s.ctx_bytes) {
+                    ws_total += real - s.ctx_bytes;
+                    s.ctx_bytes = real;
+                    peak_in_use = std::max(peak_in_use, in_use + ws_total);
+                }
+            }
             if (!ok) {
                 const Clock::time_point t1 = Clock::now();
                 for (Request &r : s.batch) {
@@ -242,6 +285,19 @@ int iwpp_server_create(iwpp_server **out, int device, size_t hbm_budget_bytes, i
             iwpp_server_destroy(s);
             return IWPP_ECUDA;
         }
+        sl.ctx_bytes = iwpp::ctx_device_bytes(sl.ctx);
+        s->ws_total += sl.ctx_bytes;
+    }
+    if (s->ws_total > hbm_budget_bytes) {
+        iwpp_server_destroy(s);
+        return IWPP_ENOMEM;
+    }
+    // the pool's high-water mark of memory in use starts from now
+    if (cudaDeviceGetDefaultMemPool(&s->pool, device) == cudaSuccess) {
+        uint64_t zero = 0;
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrUsedMemHigh, &zero);
+    } else {
+        s->pool = nullptr;
     }
     s->worker = std::thread([s] { s->run(); });
     *out = s;
@@ -265,6 +321,7 @@ int iwpp_server_submit(iwpp_server *s, const iwpp_request *req, uint64_t *ticket
         std::lock_guard<std::mutex> lock(s->mu);
         if (s->stop) return IWPP_EINVAL;
         q.ticket = s->next_ticket++;
+        s->live.insert(q.ticket);
         s->pending.push_back(q);
         ++s->submitted;
     }
@@ -276,18 +333,23 @@ int iwpp_server_submit(iwpp_server *s, const iwpp_request *req, uint64_t *ticket
 int iwpp_server_poll(iwpp_server *s, uint64_t ticket, int *status) {
     if (!s) return IWPP_EINVAL;
     std::lock_guard<std::mutex> lock(s->mu);
+    if (!s->live.count(ticket)) return IWPP_EINVAL;  // unknown or already handed out
     auto it = s->done.find(ticket);
     if (it == s->done.end()) return 0;
     if (status) *status = it->second.status;
+    s->done.erase(it);
+    s->live.erase(ticket);
     return 1;
 }
 
 int iwpp_server_wait(iwpp_server *s, uint64_t ticket, int *status, double *latency_ms) {
     if (!s) return IWPP_EINVAL;
     std::unique_lock<std::mutex> lock(s->mu);
-    if (ticket == 0 || ticket >= s->next_ticket) return IWPP_EINVAL;
+    if (!s->live.count(ticket)) return IWPP_EINVAL;  // unknown or already handed out
     s->cv_done.wait(lock, [&] { return s->done.count(ticket) != 0; });
     const Done d = s->done[ticket];
+    s->done.erase(ticket);
+    s->live.erase(ticket);
     if (status) *status = d.status;
     if (latency_ms) *latency_ms = d.latency_ms;
     return IWPP_OK;
@@ -300,8 +362,15 @@ int iwpp_server_stats(iwpp_server *s, iwpp_server_stats_t *out) {
     out->completed = s->completed;
     out->batches = s->batches;
     out->pending = s->pending.size();
-    out->bytes_in_use = s->in_use;
+    out->bytes_in_use = s->in_use + s->ws_total;
     out->peak_bytes_in_use = s->peak_in_use;
+    out->workspace_bytes = s->ws_total;
+    out->records = s->done.size();
+    out->pool_used_high = 0;
+    if (s->pool) {
+        uint64_t v = 0;
+        if (cudaMemPoolGetAttribute(s->pool, cudaMemPoolAttrUsedMemHigh, &v) == cudaSuccess) out->pool_used_high = v;
+    }
     return IWPP_OK;
 }
 

@@ -33,7 +33,7 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("iwpp_ctx_create", "iwpp_ctx_destroy", "iwpp_recon", "iwpp_edt",
                      "iwpp_recon_batched", "iwpp_edt_batched", "iwpp_recon_async", "iwpp_edt_async",
-                     "iwpp_sync", "iwpp_stats"):
+                     "iwpp_sync", "iwpp_stats", "iwpp_submit", "iwpp_poll", "iwpp_wait"):
         assert required in names
 
 

@@ -67,6 +67,28 @@ def test_many_tiles_ragged(cuda_ctx, density):
     np.testing.assert_array_equal(run(cuda_ctx, m, s), oracle.gdt(m, s))
 
 
+def test_long_valid_call_outlasts_the_wait_bound(cuda_ctx):
+    """The device-side bound (timeout_ms) is on a wait that sees no progress,
+    not on the work: a 2048^2 serpentine maze, whose one corridor is walked
+    by thousands of tile visits in sequence, runs about ten times longer than
+    timeout_ms = 50 and still completes with the exact result."""
+    import time
+
+    m, s = serpentine(2048, 2048)
+    ref = oracle.gdt(m, s)
+    old = cuda_ctx.options()
+    cuda_ctx.set_options(timeout_ms=50)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        got = run(cuda_ctx, m, s)
+        elapsed = time.perf_counter() - t0
+    finally:
+        cuda_ctx.set_options(**old)
+    assert elapsed > 0.05
+    np.testing.assert_array_equal(got, ref)
+
+
 def test_serpentine_maze_crosses_every_tile_repeatedly(cuda_ctx):
     m, s = serpentine(700, 900)
     ref = oracle.gdt(m, s)

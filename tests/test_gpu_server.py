@@ -103,21 +103,55 @@ def test_alone_equals_in_mix():
         srv.close()
 
 
-def test_budget_admission_and_oversize_request():
+def req_bytes(r):
+    """The device bytes the server counts for a request: three buffers, each
+    rounded up to 2 MiB."""
+    mb2 = 2 << 20
+    rnd = lambda n: -(-n // mb2) * mb2  # noqa: E731
+    if r["op"] == "recon":
+        return 3 * rnd(r["marker"].numel())
+    return rnd(r["binary"].numel()) + 2 * rnd(4 * r["binary"].numel())
+
+
+def test_budget_admission_counts_the_workspace_and_real_memory():
+    """The budget bounds the device memory the server really holds: the
+    memory pool's high-water mark of request images plus the resident
+    workspace of the streams' contexts.  The budget leaves room for the
+    workspace and 1.5 requests; were the workspace left out of admission,
+    all ten requests would be admitted at once and the pool's high-water
+    mark alone would break the bound."""
     reqs = make_requests(24, 10)
-    biggest = max(r["marker"].numel() * 3 if r["op"] == "recon" else r["binary"].numel() * 9 for r in reqs)
-    budget = int(biggest * 1.5) + 4096
+    # the workspace the contexts grow to on this mix (run twice, so that it
+    # has settled); one request at a time needs no more than that
+    probe = Server(0, hbm_budget=8 << 30, streams=3, max_batch=8)
+    try:
+        for _ in range(2):
+            for t in [submit(probe, r) for r in reqs]:
+                assert probe.wait(t)[0] == 0
+        ws = probe.stats()["workspace_bytes"]
+    finally:
+        probe.close()
+    biggest = max(req_bytes(r) for r in reqs)
+    assert sum(req_bytes(r) for r in reqs) > 2 * biggest
+    budget = ws + int(biggest * 1.5)
     srv = Server(0, hbm_budget=budget, streams=3, max_batch=8)
     try:
         tickets = [submit(srv, r) for r in reqs]
         for t in tickets:
             assert srv.wait(t)[0] == 0
-        assert srv.stats()["peak_bytes_in_use"] <= budget
+        st = srv.stats()
+        assert st["workspace_bytes"] <= ws
+        assert st["peak_bytes_in_use"] <= budget
+        assert st["pool_used_high"] + st["workspace_bytes"] <= budget
+        assert st["records"] == 0  # every result was handed out and dropped
         for r in reqs:
             check(r)
-        big = torch.zeros((1024, 1024), dtype=torch.uint8).pin_memory()
+        # a handed-out ticket is retired
+        with pytest.raises(Exception):
+            srv.wait(tickets[0])
+        big = torch.zeros((2048, 2048), dtype=torch.uint8).pin_memory()  # 12 MiB > 1.5 requests
         out = torch.empty_like(big)
         st, _ = srv.wait(srv.submit_recon(big, big, out))
-        assert st == -2  # larger than the whole budget
+        assert st == -2  # cannot fit next to the workspace, even alone
     finally:
         srv.close()
