@@ -80,6 +80,10 @@ typedef struct {
     uint64_t kernel_ns;        /* device time from the first to the last persistent
                                   launch of each call, summed (only while the
                                   `timing` option is set; resolved at iwpp_sync) */
+    uint64_t sweep_sets;       /* raster + anti-raster sweep sets run, summed over
+                                  tile visits                                    */
+    uint64_t revisits;         /* tile visits of tiles visited before in the same
+                                  call (tiles_processed - revisits = first visits) */
 } iwpp_stats_t;
 
 /* Tunables; iwpp_get_options() fills the defaults: tile 0, blocks_per_sm 0,

@@ -40,7 +40,7 @@ class Stats(ctypes.Structure):
         "calls", "tiles_processed", "tiles_initial", "seeds", "pushes", "spills",
         "rescans", "relaunches", "rounds", "wait_ns", "visit_ns")] +
         [("phase_ns", ctypes.c_uint64 * 4)] +
-        [(n, ctypes.c_uint64) for n in ("kernel_launches", "kernel_ns")])
+        [(n, ctypes.c_uint64) for n in ("kernel_launches", "kernel_ns", "sweep_sets", "revisits")])
 
 
 class Options(ctypes.Structure):

@@ -1224,6 +1224,8 @@ int iwpp_stats(iwpp_ctx *ctx, iwpp_stats_t *out) {
     for (int i = 0; i < 4; ++i) out->phase_ns[i] = c.phase_ns[i];
     out->kernel_launches = ctx->launches;
     out->kernel_ns = ctx->kernel_ns;
+    out->sweep_sets = c.sweep_sets;
+    out->revisits = c.revisits;
     return IWPP_OK;
 }
 
@@ -1236,6 +1238,7 @@ int iwpp_stats_reset(iwpp_ctx *ctx) {
     c.tiles_processed = c.seeds = c.pushes = c.spills = c.rescans = c.relaunches = c.rounds = 0;
     c.wait_ns = c.visit_ns = 0;
     for (int i = 0; i < 4; ++i) c.phase_ns[i] = 0;
+    c.sweep_sets = c.revisits = 0;
     CK(cudaMemcpy(ctx->ctl, &c, sizeof c, cudaMemcpyHostToDevice), "stats reset");
     ctx->calls = 0;
     ctx->tiles_initial = 0;

@@ -43,6 +43,8 @@ struct Control {
     unsigned long long wait_ns;   // summed time CTAs waited for a tile
     unsigned long long visit_ns;  // summed time CTAs spent visiting tiles
     unsigned long long phase_ns[4];  // visit phases: stage, sweep+seed, queue, store+border
+    unsigned long long sweep_sets;   // sweep sets run, summed over visits
+    unsigned long long revisits;     // visits of tiles visited before
 };
 
 // Tile queue: a linear array of `cap` slots filled once each.  Tickets

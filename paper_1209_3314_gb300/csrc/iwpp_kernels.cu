@@ -68,9 +68,10 @@ enum : int {
     H_OFF = 32,   // 9 neighbour offsets of the current layout
     H_CHG = 44,   // the visit lowered a value (watershed-family visits)
     H_PH = 48,    // 4 phase durations of the visit (ns, low 32 bits)
+    H_SETS = 52,  // sweep sets the visit ran
 };
 constexpr int HDR_BYTES = 512;  // header ints, mbarrier at byte 256, CTA counters at byte 320
-constexpr int HDR_STATS = 320;  // 10 x u64: tiles, seeds, pushes, spills, rescans, rounds, phase[4]
+constexpr int HDR_STATS = 320;  // 12 x u64: tiles, seeds, pushes, spills, rescans, rounds, phase[4], sets, revisits
 
 // byte offsets of the layouts.  The uint8 reconstruction works in its two
 // TMA boxes and keeps short block queues (overflow spills to global): its
@@ -88,6 +89,9 @@ static_assert(RU8_JW % 128 == 0 && RU8_IW % 128 == 0 && RI32_J % 128 == 0 && RI3
 static_assert(
                   BU8_PAD <= 2 * QCAP_E * 2,
               "queues must fit the staging union");
+// the distance transform's sweep change flags (320 bytes at the end of the
+// second queue buffer) must not overlap the binary box or the first buffer
+static_assert(BU8_BYTES <= 2 * QCAP_E * 2 - 320 && QCAP_E * 2 <= 2 * QCAP_E * 2 - 320, "EDT change flags");
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 // geodesic distance: D as the int32 box layout (stride 72, cell (r, c) at
@@ -155,6 +159,7 @@ __device__ __forceinline__ void begin_visit(int *hdr) {
         hdr[H_CNT0] = 0; hdr[H_CNT1] = 0; hdr[H_RESCAN] = 0;
         hdr[H_PUSH] = 0; hdr[H_SPILL] = 0; hdr[H_RESC] = 0; hdr[H_SEEDS] = 0; hdr[H_ROUNDS] = 0;
         hdr[H_PH] = hdr[H_PH + 1] = hdr[H_PH + 2] = hdr[H_PH + 3] = 0;
+        hdr[H_SETS] = 0;
     }
 }
 
@@ -636,7 +641,9 @@ __device__ void recon_propagate(const KArgs &ka, const G &g, int *hdr, uint16_t 
     RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, qcap, ka.spill_cap, ka.queue_mode & 1};
     auto sweeps_then_dilate = [&](const RQ &q, int sets) -> unsigned {
         bool changed = true;
-        for (int s = 0; s < sets && changed; ++s) changed = g.sweep(CONN);
+        int s = 0;
+        for (; s < sets && changed; ++s) changed = g.sweep(CONN);
+        if (threadIdx.x == 0) hdr[H_SETS] += s;
         // a sweep set that changed nothing proves the tile stable
         if (!changed && sets > 0) return 0u;
         return g.template dilate<CONN, NT>(q, off);
@@ -998,20 +1005,42 @@ __device__ __forceinline__ bool edt_try(unsigned *V, int oy, int ox, int pr, int
     }
 }
 
-// Best of the current feature and a candidate for pixel (y, x): the
-// strictly closer one, or the one with smaller packed coordinates when
-// equally close (the same rule as the compare-and-swap updates).
+// Best of the current feature and candidates for pixel (y, x): the strictly
+// closer one, or the one with smaller packed coordinates when equally close
+// (the same rule as the compare-and-swap updates).  The rule is one
+// lexicographic comparison of 64-bit keys (squared distance << 32 | packed
+// feature): squared distances stay below 2^31 for sides up to 32768, and
+// 'inf' is the largest key.
+__device__ __forceinline__ unsigned long long ekey(unsigned d, unsigned f) {
+    return ((unsigned long long)d << 32) | f;
+}
+constexpr unsigned long long KEY_INF = ~0ull;
+
 struct Pick {
-    unsigned best, db;
-    __device__ __forceinline__ Pick(unsigned f, int y, int x) : best(f), db(f == VR_INF ? VR_INF : d2(y, x, f)) {}
+    unsigned long long key;
+    __device__ __forceinline__ Pick(unsigned f, int y, int x) : key(f == VR_INF ? KEY_INF : ekey(d2(y, x, f), f)) {}
     __device__ __forceinline__ void consider(unsigned cand, int y, int x) {
-        if (cand == VR_INF) return;
-        const unsigned dn = d2(y, x, cand);
-        if (dn < db || (dn == db && cand < best)) {
-            best = cand;
-            db = dn;
-        }
+        if (cand != VR_INF) key = min(key, ekey(d2(y, x, cand), cand));
     }
+    // a candidate whose squared distance is already known
+    __device__ __forceinline__ void consider_d(unsigned cand, unsigned d) {
+        if (cand != VR_INF) key = min(key, ekey(d, cand));
+    }
+    __device__ __forceinline__ unsigned best() const { return (unsigned)key; }
+    __device__ __forceinline__ unsigned dist() const { return (unsigned)(key >> 32); }
+};
+
+// A running candidate of a sweep pass: feature f, its squared distance d to
+// the current pixel and the increment t to the next pixel along the pass.
+// One step along an axis changes the offset o to the feature by one, so
+// (o + 1)^2 = o^2 + (2o + 1): d grows by t, and t by 2.  When the pass
+// takes a new feature at offset o (pixel minus feature, signed along the
+// pass direction), t = 2o + 1.
+struct Run {
+    unsigned f, d;
+    int t;
+    __device__ __forceinline__ void step() { d += (unsigned)t; t += 2; }
+    __device__ __forceinline__ void take(unsigned nf, unsigned nd, int o) { f = nf; d = nd; t = 2 * o + 1; }
 };
 
 // Row pass of the distance-transform sweep (one thread per row, DIR +1
@@ -1020,13 +1049,29 @@ struct Pick {
 // propagation does.  The features are read four cells at a time with
 // 16-byte loads (cell 1 sits at word r*72 + 4): the threads of a warp own
 // rows 72 words apart, which scalar loads would put on 4 banks.  Only the
-// cells a pass improves are stored.
+// cells a pass improves are stored.  The previous pixel's feature carries
+// its squared distance along (Run), so only the pixel's own feature needs a
+// distance computation.
 template <int DIR>
-__device__ __forceinline__ bool edt_row_pass(unsigned *__restrict__ V, int r, int oy, int ox) {
+__device__ __forceinline__ bool edt_row_pass(unsigned *__restrict__ V, int r, int oy, int ox, uint8_t *RF,
+                                             uint8_t *CF) {
     const int base = r * EP + 3, y = oy + r;
     const uint4 *vp = (const uint4 *)(V + base + 1);
     bool ch = false;
-    unsigned run = V[base + (DIR > 0 ? 0 : TS + 1)];
+    const int c0 = DIR > 0 ? 0 : TS + 1;
+    Run run;
+    {
+        const unsigned f = V[base + c0];
+        if (f == VR_INF) {
+            run.f = VR_INF;
+            run.d = 0;
+            run.t = 0;
+        } else {
+            const int x = ox + c0;
+            run.take(f, d2(y, x, f), DIR * (x - (int)(f & 0xFFFFu)));
+        }
+    }
+    const unsigned self1 = pack_yx(y, ox + 1);  // cell 1; ox + 1 = x0 >= 0
 #pragma unroll 1
     for (int s = 0; s < TS / 4; ++s) {
         const int k = DIR > 0 ? s : TS / 4 - 1 - s;
@@ -1037,48 +1082,79 @@ __device__ __forceinline__ bool edt_row_pass(unsigned *__restrict__ V, int r, in
             const int jj = DIR > 0 ? j : 3 - j;
             const int c = 4 * k + jj + 1;
             const unsigned f = f4[jj];
-            if (f == pack_yx(y, ox + c)) {  // a feature is its own nearest
-                run = f;
+            run.step();
+            if (f == self1 + (unsigned)(c - 1)) {  // a feature is its own nearest
+                run.f = f;
+                run.d = 0;
+                run.t = 1;
                 continue;
             }
             Pick p(f, y, ox + c);
-            p.consider(run, y, ox + c);
-            if (p.best != f) { V[base + c] = p.best; ch = true; }
-            run = p.best;
+            p.consider_d(run.f, run.d);
+            const unsigned b = p.best();
+            if (b != f) {
+                V[base + c] = b;
+                CF[c] = 1;
+                ch = true;
+            }
+            if (b != run.f) run.take(b, p.dist(), DIR * (ox + c - (int)(b & 0xFFFFu)));
         }
     }
+    if (ch) RF[r] = 1;
     return ch;
 }
 
 // Column pass of the distance-transform sweep (DIR +1 downwards over the
 // upper neighbours, -1 upwards over the lower ones), one thread per column.
-// The vertical candidate is this thread's running feature; the diagonal
-// ones are read from shared memory, where the neighbouring columns' threads
-// may or may not have stored their new feature yet -- either is a valid
-// candidate, and keeping them off the running feature's dependency chain
-// leaves only the vertical candidate's test on it.
+// The vertical candidate is this thread's running feature, which carries
+// its squared distance along (Run); the diagonal ones are read from shared
+// memory, where the neighbouring columns' threads may or may not have
+// stored their new feature yet -- either is a valid candidate, and keeping
+// them off the running feature's dependency chain leaves only the vertical
+// candidate's test on it.
 template <int DIR>
-__device__ __forceinline__ bool edt_column_pass(unsigned *__restrict__ V, int oy, int ox, int t) {
+__device__ __forceinline__ bool edt_column_pass(unsigned *__restrict__ V, int oy, int ox, int t, uint8_t *RF,
+                                                uint8_t *CF) {
     const int c = t + 1, x = ox + c;
     const int r0 = DIR > 0 ? 0 : RR - 1;
-    unsigned up = V[ecell(r0, c)];
+    Run up;
+    {
+        const unsigned f = V[ecell(r0, c)];
+        if (f == VR_INF) {
+            up.f = VR_INF;
+            up.d = 0;
+            up.t = 0;
+        } else {
+            const int y = oy + r0;
+            up.take(f, d2(y, x, f), DIR * (y - (int)(f >> 16)));
+        }
+    }
     bool ch = false;
 #pragma unroll 2
     for (int s = 1; s <= TS; ++s) {
         const int r = DIR > 0 ? s : RR - 1 - s;
         const int i = ecell(r, c), y = oy + r, ip = i - DIR * EP;
         const unsigned f = V[i];
+        up.step();
         if (f == pack_yx(y, x)) {  // a feature is its own nearest
-            up = f;
+            up.f = f;
+            up.d = 0;
+            up.t = 1;
             continue;
         }
         Pick p(f, y, x);
         p.consider(V[ip - 1], y, x);
         p.consider(V[ip + 1], y, x);
-        p.consider(up, y, x);
-        if (p.best != f) { V[i] = p.best; ch = true; }
-        up = p.best;
+        p.consider_d(up.f, up.d);
+        const unsigned b = p.best();
+        if (b != f) {
+            V[i] = b;
+            RF[r] = 1;
+            ch = true;
+        }
+        if (b != up.f) up.take(b, p.dist(), DIR * (y - (int)(b >> 16)));
     }
+    if (ch) CF[c] = 1;
     return ch;
 }
 
@@ -1089,28 +1165,29 @@ __device__ __forceinline__ bool edt_column_pass(unsigned *__restrict__ V, int oy
 // either way; later steps use compare-and-swap and so only improve it).
 // Block-uniform "changed" result: a set that changes nothing wrote nothing,
 // so every pixel was compared with all 8 neighbours' current features and
-// the tile is stable.
+// the tile is stable.  RF[r] / CF[c] (cleared by the caller) are set for
+// every row / column in which the set wrote a pixel.
 template <int NT>
-__device__ bool edt_sweep_set(unsigned *V, int oy, int ox) {
+__device__ bool edt_sweep_set(unsigned *V, int oy, int ox, uint8_t *RF, uint8_t *CF) {
     const int t = threadIdx.x;
     bool ch = false;
     if (NT >= 2 * TS) {
         if (t < TS) {
-            ch |= edt_row_pass<+1>(V, t + 1, oy, ox);
-            ch |= edt_column_pass<+1>(V, oy, ox, t);
+            ch |= edt_row_pass<+1>(V, t + 1, oy, ox, RF, CF);
+            ch |= edt_column_pass<+1>(V, oy, ox, t, RF, CF);
         } else if (t < 2 * TS) {
-            ch |= edt_row_pass<-1>(V, t - TS + 1, oy, ox);
-            ch |= edt_column_pass<-1>(V, oy, ox, t - TS);
+            ch |= edt_row_pass<-1>(V, t - TS + 1, oy, ox, RF, CF);
+            ch |= edt_column_pass<-1>(V, oy, ox, t - TS, RF, CF);
         }
     } else {
         if (t < TS) {
-            ch |= edt_row_pass<+1>(V, t + 1, oy, ox);
-            ch |= edt_row_pass<-1>(V, t + 1, oy, ox);
+            ch |= edt_row_pass<+1>(V, t + 1, oy, ox, RF, CF);
+            ch |= edt_row_pass<-1>(V, t + 1, oy, ox, RF, CF);
         }
         __syncthreads();
         if (t < TS) {
-            ch |= edt_column_pass<+1>(V, oy, ox, t);
-            ch |= edt_column_pass<-1>(V, oy, ox, t);
+            ch |= edt_column_pass<+1>(V, oy, ox, t, RF, CF);
+            ch |= edt_column_pass<-1>(V, oy, ox, t, RF, CF);
         }
     }
     return __syncthreads_or(ch) != 0;
@@ -1121,8 +1198,19 @@ __device__ bool edt_sweep_set(unsigned *V, int oy, int ox) {
 // pixel that can still improve a neighbour is queued (a pixel that did not
 // change was seen by all its neighbours).  Each pixel is written only by its
 // own thread.
+//
+// After a sweep set, only pixels with a pixel written by that set in their
+// 3x3 neighbourhood can be improved by a neighbour: any other pixel and all
+// its neighbours kept their features through the set, whose passes compared
+// the pixel with each neighbour's feature, so none is strictly better (nor
+// equally near with smaller coordinates).  NR[r] / NC[c] (rows / columns
+// within one of a written one) select those pixels; the others are
+// skipped.  The argument for the queue holds unchanged: a skipped pixel
+// can only become improvable by a neighbour that changes in this step,
+// and that neighbour is queued.
 template <int NT>
-__device__ unsigned edt_dilate_seed(unsigned *V, int oy, int ox, const RQ &q, const int *off) {
+__device__ unsigned edt_dilate_seed(unsigned *V, int oy, int ox, const RQ &q, const int *off, const uint8_t *NR,
+                                    const uint8_t *NC) {
     unsigned pushed = 0;
     for (int base = 0; base < TS * TS; base += NT) {
         const int k = base + threadIdx.x;
@@ -1133,12 +1221,12 @@ __device__ unsigned edt_dilate_seed(unsigned *V, int oy, int ox, const RQ &q, co
             const int y = oy + r, x = ox + c;
             i = ecell(r, c);
             const unsigned f = V[i];
-            if (f != pack_yx(y, x)) {  // features stay
+            if ((NR[r] & NC[c]) && f != pack_yx(y, x)) {  // features stay
                 Pick p(f, y, x);
 #pragma unroll
                 for (int n = 0; n < 8; ++n) p.consider(V[i + off[n]], y, x);
-                if (p.best != f) {
-                    V[i] = p.best;
+                if (p.best() != f) {
+                    V[i] = p.best();
                     m = 1u << 8;
                 }
             }
@@ -1225,6 +1313,27 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
         if (need_n) stage_plain<int, BI32_W>((int *)V, jd->nearest, jd->w, jd->h, jd->w, x0 - 4, oy, NT);
         __syncthreads();
     }
+    // A first visit of a tile whose pixels are all features (inside the
+    // image) has its result already: each pixel is its own nearest feature
+    // at distance 0, and no neighbour can ever improve it, so neighbours
+    // never ask for a second visit.  Such a tile skips steps 1-3; its store
+    // and border test use its own coordinates directly.
+    bool trivial = false;
+    if (first && x0 + TS <= jd->w && y0 + TS <= jd->h) {
+        bool all = true;
+        for (int k = tid; k < TS * 4; k += NT) {  // 16-byte chunks of the interior rows
+            const uint4 b = *(const uint4 *)(BB + (k / 4 + 1) * BU8_W + 16 + (k & 3) * 16);
+            const unsigned w4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const unsigned v = w4[j];
+                // FEATURE_ZERO: every byte 0; FEATURE_NONZERO: no byte 0
+                all &= (jd->flags & 1) ? ((v - 0x01010101u) & ~v & 0x80808080u) == 0 : v == 0;
+            }
+        }
+        trivial = __syncthreads_and(all) != 0;
+    }
+    if (!trivial) {
     // 1. VR of tile + halo, converted in place: linear nearest indices of
     //    visited regions -> packed coordinates; unvisited regions from the
     //    binary image (Algorithm 6 initialisation); outside the image 'inf'
@@ -1259,11 +1368,26 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     uint16_t *spill = ka.spill + (int64_t)blockIdx.x * 2 * ka.spill_cap;
     const int qcap = (ka.queue_mode & 2) ? 0 : QCAP_E;
     RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, qcap, ka.spill_cap, ka.queue_mode & 1};
+    // change flags of the last sweep set: rows RF, columns CF; NR / NC mark
+    // the rows / columns within one of a flagged one.  They live in the
+    // second queue buffer, which is free until the propagation rounds.
+    uint8_t *RF = (uint8_t *)(sm + E_U + 2 * QCAP_E * 2 - 320), *CF = RF + 72, *NR = RF + 144, *NC = RF + 216;
     auto sweeps_then_dilate = [&]() -> unsigned {
         bool changed = true;
-        for (int s = 0; s < ka.edt_sweeps && changed; ++s) changed = edt_sweep_set<NT>(V, oy, ox);
-        if (!changed && ka.edt_sweeps > 0) return 0u;
-        return edt_dilate_seed<NT>(V, oy, ox, q0, off);
+        int s = 0;
+        for (; s < ka.edt_sweeps && changed; ++s) {
+            if (tid < RR) { RF[tid] = 0; CF[tid] = 0; }
+            __syncthreads();
+            changed = edt_sweep_set<NT>(V, oy, ox, RF, CF);
+        }
+        if (tid == 0) hdr[H_SETS] += s;
+        if (!changed) return 0u;
+        if (tid >= 1 && tid <= TS) {
+            NR[tid] = RF[tid - 1] | RF[tid] | RF[tid + 1];
+            NC[tid] = CF[tid - 1] | CF[tid] | CF[tid + 1];
+        }
+        __syncthreads();
+        return edt_dilate_seed<NT>(V, oy, ox, q0, off, NR, NC);
     };
     unsigned seeds;
     if (first && ka.edt_sweeps > 0) {
@@ -1292,6 +1416,7 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     run_rounds<NT, 8>(hdr, Q0, Q1, qcap, spill, ka.spill_cap, off, proc, rescan, deadline, ka.ctl,
                       ka.queue_mode & 1);
     __syncthreads();
+    }  // !trivial
     pc.mark(hdr, 2);
 
     // 4. store nearest (linear index) and squared distance, four pixels per
@@ -1308,7 +1433,7 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
             int nv[4], dv[4];
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const unsigned f = V[ecell(r + 1, 4 * q + b + 1)];
+                const unsigned f = trivial ? pack_yx(gy, gx + b) : V[ecell(r + 1, 4 * q + b + 1)];
                 nv[b] = f == VR_INF ? -1 : (int)(f >> 16) * jd->w + (int)(f & 0xFFFFu);
                 dv[b] = f == VR_INF ? INT_MAX : (int)d2(gy, gx + b, f);
             }
@@ -1368,7 +1493,7 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
             for (int n = 0; n < 8; ++n) {
                 const int pr = r + nb_dy(8, n), pcc = c + nb_dx(8, n);
                 if (pr < 1 || pr > TS || pcc < 1 || pcc > TS) continue;
-                const unsigned fp = V[ecell(pr, pcc)];
+                const unsigned fp = trivial ? pack_yx(oy + pr, ox + pcc) : V[ecell(pr, pcc)];
                 if (fp != VR_INF && d2(gy, gx, fp) < dq) need = true;
             }
             if (need) hdr[H_FLAG + reg] = 1;
@@ -1607,7 +1732,9 @@ __device__ bool gdt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     RQ q0{Q0, spill, hdr + H_CNT0, hdr + H_RESCAN, qcap, ka.spill_cap, ka.queue_mode & 1};
     auto sweeps_then_seed = [&]() -> unsigned {
         bool changed = true;
-        for (int s = 0; s < ka.gdt_sweeps && changed; ++s) changed = gdt_sweep_set(D, M);
+        int s = 0;
+        for (; s < ka.gdt_sweeps && changed; ++s) changed = gdt_sweep_set(D, M);
+        if (tid == 0) hdr[H_SETS] += s;
         if (!changed && ka.gdt_sweeps > 0) return 0u;
         return gdt_dilate_seed<NT>(D, M, q0, off);
     };
@@ -1971,7 +2098,7 @@ __global__ void __launch_bounds__(FAM_NT[FAM], FAM_MINB[FAM]) persistent_kernel(
     if (ld_volatile(&ka.ctl->done)) return;
     unsigned long long *cst = (unsigned long long *)(smem + HDR_STATS);
     if (threadIdx.x == 0) mbar_init(bar, 1);
-    if (threadIdx.x < 10) cst[threadIdx.x] = 0;
+    if (threadIdx.x < 12) cst[threadIdx.x] = 0;
     __syncthreads();
     uint32_t phase = 0;
     unsigned long long t_wait = 0, t_visit = 0;
@@ -2032,6 +2159,8 @@ __global__ void __launch_bounds__(FAM_NT[FAM], FAM_MINB[FAM]) persistent_kernel(
             cst[4] += (unsigned)hdr[H_RESC];
             cst[5] += (unsigned)hdr[H_ROUNDS];
             for (int i = 0; i < 4; ++i) cst[6 + i] += (unsigned)hdr[H_PH + i];
+            cst[10] += (unsigned)hdr[H_SETS];
+            cst[11] += hdr[H_SRC + 4] != 0 ? 1u : 0u;  // the tile had been visited before
         }
         __syncthreads();
     }
@@ -2045,6 +2174,8 @@ __global__ void __launch_bounds__(FAM_NT[FAM], FAM_MINB[FAM]) persistent_kernel(
         atomicAdd(&ka.ctl->rescans, cst[4]);
         atomicAdd(&ka.ctl->rounds, cst[5]);
         for (int i = 0; i < 4; ++i) atomicAdd(&ka.ctl->phase_ns[i], cst[6 + i]);
+        atomicAdd(&ka.ctl->sweep_sets, cst[10]);
+        atomicAdd(&ka.ctl->revisits, cst[11]);
     }
 }
 
