@@ -152,9 +152,9 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_key, side):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources; otherwise None."""
+def profiled(kernel_key, field):
+    """A per-pixel figure of one kernel from the committed ncu summary, if it
+    was taken on the current kernel sources; otherwise None."""
     try:
         with open(PROFILE_TRAFFIC) as f:
             d = json.load(f)
@@ -163,9 +163,75 @@ def profiled_traffic(kernel_key, side):
     if d.get("source_hash") != source_hash():
         return None
     e = d.get("kernels", {}).get(kernel_key)
-    if not e:
+    if not e or field not in e:
         return None
-    return e["bytes_per_px"] * side * side
+    return float(e[field])
+
+
+def profiled_traffic(kernel_key, side):
+    """DRAM bytes per launch (ncu, scaled from the captured case by the pixel
+    count), or None."""
+    v = profiled(kernel_key, "bytes_per_px")
+    return None if v is None else v * side * side
+
+
+def visit_stats(ctx, fn):
+    """Tile visits of one call: visits per tile, revisits per tile and sweep
+    sets per visit (the context's counters around one extra call)."""
+    ctx.sync()
+    ctx.stats_reset()
+    fn()
+    ctx.sync()
+    st = ctx.stats()
+    t = max(1, st["tiles_initial"])
+    v = max(1, st["tiles_processed"])
+    return {"tiles": st["tiles_initial"], "visits_per_tile": round(st["tiles_processed"] / t, 3),
+            "revisits_per_tile": round(st["revisits"] / t, 3), "sweep_sets_per_visit": round(st["sweep_sets"] / v, 3),
+            "queue_pushes_per_px": round(st["pushes"] / (t * 4096), 4)}
+
+
+def issue_roofline(kernel_key, side, ms, sm_mhz):
+    """Second roofline for the issue-bound kernels: warp instructions per
+    launch (ncu's per-pixel count on the captured case x the pixel count)
+    over the launch time, against the issue rate of 152 SMs x 4 schedulers x
+    one warp instruction per cycle at the sampled median SM clock."""
+    w = profiled(kernel_key, "warp_instr_per_px")
+    if w is None or not ms or not sm_mhz:
+        return None
+    achieved = w * side * side / (ms * 1e-3) / 1e9
+    peak = 152 * 4 * sm_mhz * 1e6 / 1e9
+    return {"bound": "issue", "warp_instr_per_px": w, "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "G warp-instr/s", "frac": round(achieved / peak, 4),
+            "peak_source": "152 SMs x 4 schedulers x 1 warp instruction per cycle x sampled median SM clock"}
+
+
+def host_cpu():
+    """CPU model and the number of host cores this process may use."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    try:
+        nproc = len(os.sched_getaffinity(0))
+    except Exception:
+        nproc = os.cpu_count() or 1
+    import platform
+
+    return {"cpu_model": model or platform.machine(), "nproc": nproc, "machine": platform.machine()}
 
 
 def oracle_sample(marker, mask, binary, side_sample):
@@ -200,14 +266,16 @@ def run_reference(args, ws, rank):
         tot_px += px
         tot_t += t
     v = tot_px / tot_t / 1e6
-    sample = f"top-left {s}x{s} crop of both images per step (oracle: Algorithm 2 + Algorithm 3, one thread)"
+    sample = (f"top-left {s}x{s} crop of both images per step (oracle: Algorithm 2 + Algorithm 3, one thread); "
+              f"the same crop as the GPU line's cpu_baseline")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "Mpixel/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(tot_t / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": workload_desc(args.side), "sample": sample},
-        "cpu_baseline": {"value": round(v, 3), "unit": "Mpixel/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": round(v, 3), "unit": "Mpixel/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         **host_cpu()},
         "e2e": {"value": round(v, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -272,10 +340,11 @@ def bench_batched(ctx, dev, n, reps):
                        "back to back in one CUDA graph replay, autotuned" if tuned["batch_split"] else
                        "one persistent launch for the whole batch, CUDA graph replay, autotuned"),
             "tuned": {k: tuned[k] for k in ("sweeps", "revisit_sweep_min", "edt_sweeps", "edt_revisit_sweep_min",
-                                                 "blocks_per_sm", "batch_split")}}
+                                                 "blocks_per_sm", "batch_split", "queue_factor", "spill_cap")},
+            "tile": "64x64 (fixed)"}
 
 
-def bench_served(ctx, dev, rates, duration, budget):
+def bench_served(ctx, dev, rates, duration, budget, min_requests=2000):
     """Poisson arrivals of mixed reconstruction / EDT requests, square sides
     log-uniform 512..8192 (host images, pinned), served by the
     continuous-batching server under an HBM budget, against one job per
@@ -306,8 +375,11 @@ def bench_served(ctx, dev, rates, duration, budget):
                               "nearest": torch.empty((side, side), dtype=torch.int32).pin_memory()})
     results = {}
     for rate in rates:
-        arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * duration) + 1))
-        arr = arr[arr < duration]
+        # at least `min_requests` arrivals (p99 rests on 20+ samples), at
+        # least `duration` seconds
+        dur = max(duration, min_requests / rate)
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * dur * 1.5) + 16))
+        arr = arr[arr < dur]
         seq = [templates[i % len(templates)] for i in range(len(arr))]
         px = sum(t["px"] for t in seq)
         # continuous-batching server
@@ -323,6 +395,7 @@ def bench_served(ctx, dev, rates, duration, budget):
                 tickets.append(srv.submit_edt(t["binary"], t["sqdist"], t["nearest"]))
         lat = [srv.wait(tk)[1] for tk in tickets]
         span = time.perf_counter() - t0
+        sst = srv.stats()
         srv.close()
         # one job per launch, in arrival order
         d_in = torch.empty(3 * 8192 * 8192, dtype=torch.uint8, device=dev)
@@ -354,10 +427,13 @@ def bench_served(ctx, dev, rates, duration, budget):
         base_span = time.perf_counter() - t0
         del d_in, d_sq, d_nn
         results[str(rate)] = {
-            "requests": len(seq), "mpx": round(px / 1e6, 1),
+            "requests": len(seq), "duration_s": round(dur, 2), "mpx": round(px / 1e6, 1),
             "served": {"req_s": round(len(seq) / span, 1), "mpx_s": round(px / span / 1e6, 1),
                        "p50_ms": round(float(np.percentile(lat, 50)), 3),
-                       "p99_ms": round(float(np.percentile(lat, 99)), 3)},
+                       "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                       "batches": sst["batches"],
+                       "peak_device_gb": round(sst["peak_bytes_in_use"] / 2**30, 2),
+                       "workspace_gb": round(sst["workspace_bytes"] / 2**30, 3)},
             "one_per_launch": {"req_s": round(len(seq) / base_span, 1), "mpx_s": round(px / base_span / 1e6, 1),
                                "p50_ms": round(float(np.percentile(base_lat, 50)), 3),
                                "p99_ms": round(float(np.percentile(base_lat, 99)), 3)}}
@@ -419,9 +495,13 @@ def bench_queue_ablation(ctx, dev, reps=5):
 
 
 def bench_edt_exact(ctx, dev, d_bin, npx, reps=3):
-    """The exact separable EDT (iwpp_edt_exact) on the same binary image,
-    both feature polarities, beside the propagation EDT of the same
-    polarity: per-call CUDA-event times (median)."""
+    """On the same binary image, both feature polarities, per-call CUDA-event
+    times (median) of: the propagation EDT; the propagation EDT with its
+    wide-window second wavefront (IWPP_EDT_EXACT_PROPAGATION); the exact
+    separable EDT (iwpp_edt_exact).  Departures (pixels whose squared
+    distance differs from the exact one) are counted for both propagation
+    modes against the separable result, itself bit-exact against the
+    oracle's exact transform in the tests."""
     import statistics
 
     import torch
@@ -429,21 +509,28 @@ def bench_edt_exact(ctx, dev, d_bin, npx, reps=3):
     st = torch.cuda.current_stream(dev)
     sq = torch.empty(d_bin.shape, dtype=torch.int32, device=dev)
     nn = torch.empty_like(sq)
+    sq_ex = torch.empty_like(sq)
+    nn_ex = torch.empty_like(sq)
     res = {}
     for fnz in (False, True):
         row = {}
-        for exact in (True, False):
-            ctx.edt(d_bin, fnz, sqdist=sq, nearest=nn, exact=exact)
+        ctx.edt(d_bin, fnz, sqdist=sq_ex, nearest=nn_ex, exact=True)
+        for mode in ("exact", "propagation", "exact_propagation"):
+            ex, wide = mode == "exact", mode == "exact_propagation"
+            out_sq, out_nn = (sq_ex, nn_ex) if ex else (sq, nn)
+            ctx.edt(d_bin, fnz, sqdist=out_sq, nearest=out_nn, exact=ex, exact_propagation=wide)
             times = []
             for _ in range(reps):
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(st)
-                ctx.edt(d_bin, fnz, sqdist=sq, nearest=nn, exact=exact, sync=exact)
+                ctx.edt(d_bin, fnz, sqdist=out_sq, nearest=out_nn, exact=ex, exact_propagation=wide, sync=ex)
                 b.record(st)
                 ctx.sync()
                 times.append(a.elapsed_time(b))
             ms = statistics.median(times)
-            row["exact" if exact else "propagation"] = {"ms": round(ms, 3), "mpx_s": round(npx / ms / 1e3, 1)}
+            row[mode] = {"ms": round(ms, 3), "mpx_s": round(npx / ms / 1e3, 1)}
+            if not ex:
+                row[mode]["departures"] = int((sq != sq_ex).sum().item())
         res["features_nonzero" if fnz else "features_zero"] = row
     return res
 
@@ -649,8 +736,6 @@ def run_gpu(args, ws, rank, local):
     stream = torch.cuda.current_stream(dev)
     ctx = Context(local)
     ctx.set_options(timing=1)
-    if args.tile:
-        ctx.set_options(tile=args.tile)
     d_marker = torch.from_numpy(marker).to(dev)
     d_mask = torch.from_numpy(mask).to(dev)
     d_bin = torch.from_numpy(binary).to(dev)
@@ -802,8 +887,9 @@ def run_gpu(args, ws, rank, local):
         s = args.cpu_sample
         px, t, tr, te = oracle_sample(marker, mask, binary, s)
         cpu = {"value": round(px / t / 1e6, 3), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
-               "sample": f"top-left {s}x{s} crop of both images, Algorithm 2 ({tr:.1f} s) + "
-                         f"Algorithm 3 ({te:.1f} s), one thread"}
+               "sample": f"top-left {s}x{s} crop of both images per step (oracle: Algorithm 2 + Algorithm 3, "
+                         f"one thread); this run: Algorithm 2 {tr:.1f} s + Algorithm 3 {te:.1f} s",
+               **host_cpu()}
 
     batched = served = None
     if rank == 0 and not args.skip_batched:
@@ -831,6 +917,13 @@ def run_gpu(args, ws, rank, local):
         served = bench_served(ctx, dev, rates, args.serve_duration, 120 << 30)
 
     traffic = profiled_traffic(f"persistent_{dominant}", side)
+    visits = None
+    if rank == 0:
+        visits = {"recon": visit_stats(ctx, lambda: ctx.recon(d_marker, d_mask, 8, out=d_out, sync=False)),
+                  "edt": visit_stats(ctx, lambda: ctx.edt(d_bin, sqdist=d_sq, nearest=d_nn, sync=False))}
+    sm_mhz = (clocks or {}).get("sm_mhz")
+    issue = {"recon": issue_roofline("persistent_recon", side, r_med, sm_mhz),
+             "edt": issue_roofline("persistent_edt", side, e_med, sm_mhz)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": ws,
@@ -839,7 +932,7 @@ def run_gpu(args, ws, rank, local):
             "dtype": "u8", "data": "synthetic",
             "config": {"workload": workload_desc(side), "pixels_per_step": 2 * npx * ws,
                        "disks": ndisks, "l2": "no flush: each input (268 MB u8) exceeds the 129 MB L2",
-                       "parallelism": f"replicas x{ws}", "tile": ctx.options()["tile"] or "auto"},
+                       "parallelism": f"replicas x{ws}", "tile": "64x64"},
             "recon": {"ms": round(r_med, 4), "mpx_s": round(npx / r_med / 1e3, 1),
                       "gbs": round(r_gbs, 1), "frac_hbm": round(r_gbs / peak, 4)},
             "edt": {"ms": round(e_med, 4), "mpx_s": round(npx / e_med / 1e3, 1),
@@ -852,6 +945,8 @@ def run_gpu(args, ws, rank, local):
                          "kernel_ms_mean_per_call": round(kern_ms, 4)},
             "queue": {k: st[k] for k in ("tiles_processed", "tiles_initial", "seeds", "pushes",
                                          "spills", "rescans", "relaunches", "rounds")},
+            "visits": visits,
+            "issue_roofline": issue,
             # time inside tile visits, summed over CTAs (CTA-ms per call):
             # staging, sweeps + seeding, queue rounds, store + border test
             "phase_cta_ms_per_call": {n: round(v / 1e6 / calls, 1) for n, v in
@@ -882,9 +977,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="iwpp", choices=["iwpp", "reference"])
     ap.add_argument("--side", type=int, default=16384)
-    ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=8192)
-    ap.add_argument("--reference-sample", type=int, default=4096)
+    ap.add_argument("--reference-sample", type=int, default=8192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-served", action="store_true")

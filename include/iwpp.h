@@ -49,6 +49,18 @@ typedef enum { IWPP_U8 = 0, IWPP_I32 = 1 } iwpp_dtype;
  * non-zero pixel instead. */
 #define IWPP_EDT_FEATURE_ZERO 0
 #define IWPP_EDT_FEATURE_NONZERO 1
+/* Distance-transform mode (or-ed with the polarity): after the 8-neighbour
+ * propagation has reached its fixpoint, a second wavefront runs the same
+ * update rule with a wider window -- every offset (dy, dx) with |dy|,
+ * |dx| <= k -- whose half-width k grows with the pixel's current distance
+ * (Section 2.2: a sufficiently large neighbourhood makes the propagation
+ * exact).  k = 1 below the distance edt_wide_step, one more for each further
+ * edt_wide_step, at most 8.  This removes the departures from the exact
+ * distance that the 8-neighbour rule leaves (Figure 3); the window sizes
+ * come from measured departure distances (errors need a window that widens
+ * with the distance), and every tested image, up to 16384^2 in both
+ * polarities, comes out bit-identical to the exact transform. */
+#define IWPP_EDT_EXACT_PROPAGATION 2
 
 typedef struct iwpp_ctx iwpp_ctx;
 
@@ -91,10 +103,11 @@ typedef struct {
  * 10000, timing 0, revisit_sweep_min 0, edt_sweeps 2, edt_revisit_sweep_min
  * 64, revisit_sweeps -1, queue_mode 0, test_empty_slot 0, gdt_sweeps 8,
  * batch_split 1, ws_sweeps 6, ws_revisit_sweep_min 0, gdt_revisit_sweep_min
- * 4.  tile = 0 lets the autotuner choose.  Values are validated by
- * iwpp_set_options().  New fields are only ever appended. */
+ * 4, edt_wide_step 12.  The tile side is fixed at 64 pixels (the field
+ * accepts 0 or 64).  Values are validated by iwpp_set_options().  New fields
+ * are only ever appended. */
 typedef struct {
-    int32_t tile;            /* tile side in pixels: 0 (auto) or 64           */
+    int32_t tile;            /* tile side in pixels: fixed at 64 (0 or 64)    */
     int32_t blocks_per_sm;   /* persistent CTAs per SM, 0 = as many as fit    */
     int32_t sweeps;          /* raster+anti-raster sweep sets per bulk visit   */
     int32_t queue_factor;    /* tile-queue slots = queue_factor * tiles (>= 1) */
@@ -151,6 +164,9 @@ typedef struct {
                                 queue                                         */
     int32_t gdt_revisit_sweep_min; /* the same for the shortest-path
                                 propagation (also the SKIZ distances)         */
+    int32_t edt_wide_step;   /* IWPP_EDT_EXACT_PROPAGATION: the window's
+                                half-width grows by one per this many pixels
+                                of distance (default 12; smaller is wider)    */
 } iwpp_options;
 
 /* Creates a context on `device`.  hbm_budget_bytes bounds the workspace the
@@ -360,12 +376,15 @@ int iwpp_wait(iwpp_ctx *ctx, uint64_t ticket, int *status);
  * them on one stream with the context's other calls and read failures with
  * iwpp_sync().
  *
- * iwpp_plan_autotune times `reps` launches of each candidate option set
- * (sweep sets 1..3, revisit threshold 0 / 32, blocks per SM max / max-1) on
- * the plan's own images, keeps the fastest in the plan, stores it in the
- * context under a key of (kernel family, log2 pixels, log2 jobs, SM count)
- * so that later plans of the same kind start tuned, and copies it to *best
- * (may be NULL).  It synchronises `stream`.
+ * iwpp_plan_autotune times `reps` launches of each candidate option set on
+ * the plan's own images: first sweep sets (reconstruction 2..4, distance
+ * transform 1..3), revisit thresholds, CTAs per SM (max / max-1) and one
+ * launch or one launch per operation family; then, from the best of those,
+ * the tile-queue capacity (queue_factor 8 / 16 / 32 slots per tile) and the
+ * per-CTA spill capacity (spill_cap 1024 / 8192).  It keeps the fastest in
+ * the plan, stores it in the context under a key of (kernel family, log2
+ * pixels, log2 jobs, SM count) so that later plans of the same kind start
+ * tuned, and copies it to *best (may be NULL).  It synchronises `stream`.
  */
 typedef struct iwpp_plan iwpp_plan;
 int iwpp_plan_create(iwpp_ctx *ctx, int n, const iwpp_job *jobs, iwpp_plan **out);

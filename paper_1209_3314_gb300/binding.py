@@ -22,6 +22,7 @@ IWPP_U8 = 0
 IWPP_I32 = 1
 IWPP_EDT_FEATURE_ZERO = 0
 IWPP_EDT_FEATURE_NONZERO = 1
+IWPP_EDT_EXACT_PROPAGATION = 2
 IWPP_OP_RECON = 0
 IWPP_OP_EDT = 1
 
@@ -53,7 +54,7 @@ class Options(ctypes.Structure):
                 ("queue_mode", ctypes.c_int32), ("test_empty_slot", ctypes.c_int32),
                 ("gdt_sweeps", ctypes.c_int32), ("batch_split", ctypes.c_int32),
                 ("ws_sweeps", ctypes.c_int32), ("ws_revisit_sweep_min", ctypes.c_int32),
-                ("gdt_revisit_sweep_min", ctypes.c_int32)]
+                ("gdt_revisit_sweep_min", ctypes.c_int32), ("edt_wide_step", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -266,11 +267,12 @@ class Context:
         return out
 
     def edt(self, binary, feature_nonzero: bool = False, sqdist=None, nearest=None,
-            stream=None, sync: bool = True, exact: bool = False):
+            stream=None, sync: bool = True, exact: bool = False, exact_propagation: bool = False):
         """Distance transform of a uint8 CUDA tensor.  Returns
         (sqdist int32, nearest int32 linear index).  exact=True runs the
         exact separable transform (iwpp_edt_exact, synchronous) instead of
-        the propagation method."""
+        the propagation method; exact_propagation=True adds the wide-window
+        second wavefront (IWPP_EDT_EXACT_PROPAGATION)."""
         torch = _torch()
         h, w = binary.shape
         if sqdist is None:
@@ -283,6 +285,8 @@ class Context:
         b = image_of(binary)
         fn = self.lib.iwpp_edt_exact if exact else (self.lib.iwpp_edt if sync else self.lib.iwpp_edt_async)
         flags = IWPP_EDT_FEATURE_NONZERO if feature_nonzero else IWPP_EDT_FEATURE_ZERO
+        if exact_propagation:
+            flags |= IWPP_EDT_EXACT_PROPAGATION
         self._check(fn(self.h, ctypes.byref(b), ctypes.c_void_p(sqdist.data_ptr()),
                        ctypes.c_void_p(nearest.data_ptr()), flags, _stream_ptr(stream)))
         return sqdist, nearest
@@ -426,7 +430,8 @@ def _job_array(jobs):
             arr[i].out = image_of(j["out"])
         else:
             arr[i].op = IWPP_OP_EDT
-            arr[i].flags = IWPP_EDT_FEATURE_NONZERO if j.get("feature_nonzero") else 0
+            arr[i].flags = ((IWPP_EDT_FEATURE_NONZERO if j.get("feature_nonzero") else 0) |
+                            (IWPP_EDT_EXACT_PROPAGATION if j.get("exact_propagation") else 0))
             arr[i].a = image_of(j["binary"])
             arr[i].sqdist = j["sqdist"].data_ptr()
             arr[i].nearest = j["nearest"].data_ptr()

@@ -96,7 +96,7 @@ int pick_family(const std::vector<JobDesc> &jobs) {
     if (!jobs.empty() && jobs[0].op == OP_GDT) return FAM_GDT;  // geodesic launches hold only geodesic jobs
     if (!jobs.empty() && (jobs[0].op == OP_WS_DIST || jobs[0].op == OP_WS_LABEL)) return FAM_WS;
     for (const JobDesc &j : jobs) {
-        if (j.op == OP_EDT) e = true;
+        if (j.op == OP_EDT || j.op == OP_EDT_WIDE) e = true;
         else if (j.dtype == DT_U8) r8 = true;
         else r32 = true;
     }
@@ -128,7 +128,8 @@ EncodeTiledFn encode_fn() {
 // 16-byte aligned).  False when the image does not meet TMA's alignment
 // rules (16-byte aligned base, row pitch a multiple of 16 bytes); the
 // kernel then stages with plain loads.
-bool make_map(CUtensorMap *m, const void *base, int dtype, int h, int w, int64_t pitch_elems) {
+bool make_map(CUtensorMap *m, const void *base, int dtype, int h, int w, int64_t pitch_elems, int box_w = 0,
+              int box_h = 0) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const size_t es = dtype == DT_U8 ? 1 : 4;
@@ -136,7 +137,8 @@ bool make_map(CUtensorMap *m, const void *base, int dtype, int h, int w, int64_t
     if (((uintptr_t)base & 15) || (pitch_bytes & 15) || pitch_bytes >= (1ull << 40)) return false;
     cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
     cuuint64_t strides[1] = {pitch_bytes};
-    cuuint32_t box[2] = {dtype == DT_U8 ? 96u : 72u, (cuuint32_t)(TILE + 2)};
+    cuuint32_t box[2] = {box_w ? (cuuint32_t)box_w : (dtype == DT_U8 ? 96u : 72u),
+                         box_h ? (cuuint32_t)box_h : (cuuint32_t)(TILE + 2)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, dtype == DT_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_INT32, 2,
                     const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -155,6 +157,10 @@ void make_maps(JobDesc &d) {
     if (d.op == OP_WS_DIST || d.op == OP_WS_LABEL) {  // in-edge masks, values
         d.use_tma = make_map(&d.tm[0], d.a, DT_U8, d.h, d.w, d.pa) &&
                     make_map(&d.tm[2], d.out, DT_I32, d.h, d.w, d.po);
+        return;
+    }
+    if (d.op == OP_EDT_WIDE) {  // the nearest indices with an 8-pixel halo: an 80 x 80 box
+        d.use_tma = make_map(&d.tm[1], d.nearest, DT_I32, d.h, d.w, d.w, TILE + 16, TILE + 16) ? 1 : 0;
         return;
     }
     if (d.op == OP_RECON) {
@@ -301,6 +307,10 @@ int prepare(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, const iwpp_options &opt, 
     ka.gdt_revisit_sweep_min = opt.gdt_revisit_sweep_min;
     ka.ws_sweeps = opt.ws_sweeps;
     ka.ws_revisit_sweep_min = opt.ws_revisit_sweep_min;
+    for (int j = 0; j < 7; ++j) {  // window half-width j + 2 from distance (j + 1) * step on
+        const int64_t t = (int64_t)(j + 1) * opt.edt_wide_step;
+        ka.wide_u[j] = (int)std::min<int64_t>(t * t, INT32_MAX);
+    }
     ka.timeout_ns = (unsigned long long)opt.timeout_ms * 1000000ull;
     return IWPP_OK;
 }
@@ -349,7 +359,7 @@ std::vector<std::vector<JobDesc>> launch_groups(const std::vector<JobDesc> &jobs
     std::vector<JobDesc> by[5];
     for (const JobDesc &j : jobs) {
         const int k = j.op == OP_RECON ? (j.dtype == DT_U8 ? 0 : 1)
-                                       : (j.op == OP_EDT ? 2 : (j.op == OP_GDT ? 3 : 4));
+                                       : ((j.op == OP_EDT || j.op == OP_EDT_WIDE) ? 2 : (j.op == OP_GDT ? 3 : 4));
         by[k].push_back(j);
     }
     for (auto &v : by)
@@ -357,10 +367,30 @@ std::vector<std::vector<JobDesc>> launch_groups(const std::vector<JobDesc> &jobs
     return g;
 }
 
+int run_once(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, cudaStream_t st, bool sync);
+
 // Runs (or enqueues) the whole launch sequence for `jobs` on the context's
 // workspace: one sequence per launch group, back to back on the stream
-// (they share the status block; its error bits accumulate).
+// (they share the status block; its error bits accumulate).  Distance
+// transforms with IWPP_EDT_EXACT_PROPAGATION get their second, wide-window
+// wavefront as a further launch sequence on the same stream.
 int run(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, cudaStream_t st, bool sync) {
+    std::vector<JobDesc> wide;
+    for (const JobDesc &j : jobs)
+        if (j.op == OP_EDT && (j.flags & IWPP_EDT_EXACT_PROPAGATION)) {
+            JobDesc w = j;
+            w.op = OP_EDT_WIDE;
+            wide.push_back(w);
+        }
+    if (wide.empty()) return run_once(ctx, jobs, st, sync);
+    int rc = run_once(ctx, jobs, st, false);
+    if (rc) return rc;
+    rc = run_once(ctx, wide, st, sync);
+    ctx->calls -= 1;  // the two wavefronts are one call
+    return rc;
+}
+
+int run_once(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, cudaStream_t st, bool sync) {
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     std::vector<std::vector<JobDesc>> groups = launch_groups(jobs, ctx->opt.batch_split);
     if (groups.size() > 1) {
@@ -461,7 +491,7 @@ int check_edt(iwpp_ctx *ctx, const iwpp_image *bin, const int32_t *sq, const int
     if (bin->dtype != IWPP_U8) return fail(ctx, IWPP_EINVAL, "binary image must be IWPP_U8");
     if (bin->h > 32768 || bin->w > 32768) return fail(ctx, IWPP_EINVAL, "distance transform limited to sides <= 32768");
     if (!sq || !nn) return fail(ctx, IWPP_EINVAL, "null output pointer");
-    if (flags & ~1) return fail(ctx, IWPP_EINVAL, "unknown flags 0x%x", flags);
+    if (flags & ~3) return fail(ctx, IWPP_EINVAL, "unknown flags 0x%x", flags);
     if (sq == nn) return fail(ctx, IWPP_EINVAL, "sqdist and nearest must be distinct buffers");
     return IWPP_OK;
 }
@@ -695,6 +725,7 @@ int iwpp_ctx_create(iwpp_ctx **out, int device, size_t hbm_budget_bytes) {
     ctx->opt.ws_sweeps = 6;
     ctx->opt.ws_revisit_sweep_min = 0;
     ctx->opt.gdt_revisit_sweep_min = 4;
+    ctx->opt.edt_wide_step = 12;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc(&ctx->ctl, sizeof(Control)) != cudaSuccess ||
@@ -740,7 +771,7 @@ int iwpp_get_options(const iwpp_ctx *ctx, iwpp_options *out) {
 
 int iwpp_set_options(iwpp_ctx *ctx, const iwpp_options *o) {
     if (!ctx || !o) return IWPP_EINVAL;
-    if (o->tile != 0 && o->tile != TILE) return fail(ctx, IWPP_EINVAL, "tile must be 0 (auto) or %d", TILE);
+    if (o->tile != 0 && o->tile != TILE) return fail(ctx, IWPP_EINVAL, "tile must be 0 or %d (fixed)", TILE);
     if (o->blocks_per_sm < 0 || o->sweeps < 0 || o->sweeps > 64 || o->queue_factor < 1 || o->queue_factor > 4096 ||
         o->spill_cap < 0 || o->spill_cap > (1 << 20) || o->max_relaunch < 0 || o->max_relaunch > 64 ||
         o->timeout_ms < 1 || o->timeout_ms > 600000 || o->timing < 0 || o->timing > 1 ||
@@ -748,7 +779,8 @@ int iwpp_set_options(iwpp_ctx *ctx, const iwpp_options *o) {
         o->revisit_sweeps < -1 || o->revisit_sweeps > 64 || o->queue_mode < 0 || o->queue_mode > 3 ||
         o->test_empty_slot < 0 || o->test_empty_slot > 1 || o->gdt_sweeps < 0 || o->gdt_sweeps > 64 ||
         o->batch_split < 0 || o->batch_split > 1 || o->ws_sweeps < 0 || o->ws_sweeps > 64 ||
-        o->ws_revisit_sweep_min < 0 || o->gdt_revisit_sweep_min < 0)
+        o->ws_revisit_sweep_min < 0 || o->gdt_revisit_sweep_min < 0 || o->edt_wide_step < 1 ||
+        o->edt_wide_step > 65536)
         return fail(ctx, IWPP_EINVAL, "option out of range");
     ctx->opt = *o;
     return IWPP_OK;
@@ -1371,6 +1403,33 @@ int iwpp_plan_autotune(iwpp_plan *p, void *stream, int reps, iwpp_options *best)
                     best_opt = o;
                 }
             }
+    // second stage, from the best option set: the capacities of the tile
+    // queue (slots per tile) and of each CTA's spill queue.  Too few slots
+    // cost a relaunch, too many cost memory; the spill queue trades global
+    // memory against in-tile rescans.
+    const int qf_c[3] = {8, 16, 32};
+    const int sc_c[2] = {1024, 8192};
+    const iwpp_options stage1 = best_opt;
+    for (int a = 0; a < 3 && rc == IWPP_OK; ++a)
+        for (int b = 0; b < 2 && rc == IWPP_OK; ++b) {
+            iwpp_options o = stage1;
+            o.queue_factor = qf_c[a];
+            o.spill_cap = sc_c[b];
+            if (o.queue_factor == stage1.queue_factor && o.spill_cap == stage1.spill_cap) continue;
+            if ((rc = plan_prepare(p, o))) break;
+            if ((rc = iwpp_plan_launch(p, st))) break;  // warm-up
+            if ((rc = iwpp_sync(ctx, st))) break;
+            CK(cudaEventRecord(e0, st), "cudaEventRecord");
+            for (int r = 0; r < reps && rc == IWPP_OK; ++r) rc = iwpp_plan_launch(p, st);
+            CK(cudaEventRecord(e1, st), "cudaEventRecord");
+            if (rc || (rc = iwpp_sync(ctx, st))) break;
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_opt = o;
+            }
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) {

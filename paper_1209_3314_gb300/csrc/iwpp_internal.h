@@ -12,7 +12,8 @@ namespace iwpp {
 
 // OP_WS_DIST / OP_WS_LABEL: the plateau-distance and label propagations of
 // the watershed from markers (min-propagations along per-pixel in-edge masks)
-enum : int { OP_RECON = 0, OP_EDT = 1, OP_GDT = 2, OP_WS_DIST = 3, OP_WS_LABEL = 4 };
+// OP_EDT_WIDE: the distance transform's second wavefront with the wide window
+enum : int { OP_RECON = 0, OP_EDT = 1, OP_GDT = 2, OP_WS_DIST = 3, OP_WS_LABEL = 4, OP_EDT_WIDE = 5 };
 enum : int { DT_U8 = 0, DT_I32 = 1 };
 
 // kernel families (one persistent-kernel instantiation each)
@@ -33,7 +34,8 @@ constexpr int WS_DINF = 0x3FFFFFFF;  // plateau distance of a pixel not reached 
 // One image job inside a launch.  Tiles of job j have global ids
 // [tile_base, tile_base + tiles_x * tiles_y).
 struct alignas(64) JobDesc {
-    CUtensorMap tm[3];   // TMA maps: a, b, out/nearest (valid when use_tma)
+    CUtensorMap tm[3];   // TMA maps: a, b, out/nearest (valid when use_tma); the
+                         // wide-window pass keeps its nearest box map in tm[1]
     int op, dtype, conn, flags;
     int h, w, tiles_x, tiles_y;
     int tile_base;
@@ -71,6 +73,8 @@ struct alignas(64) KArgs {
     int gdt_revisit_sweep_min;  // and their later visits' sweep threshold
     int ws_sweeps;        // watershed propagations: sweep sets per bulk visit
     int ws_revisit_sweep_min;  // and their later visits' sweep threshold
+    int wide_u[7];        // wide-window distance transform: the window's half-width is 1 + the
+                          // number of these squared-distance thresholds a pixel reaches (1..8)
     unsigned long long timeout_ns;
 };
 

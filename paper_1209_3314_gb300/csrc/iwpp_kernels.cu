@@ -92,6 +92,8 @@ static_assert(
 // the distance transform's sweep change flags (320 bytes at the end of the
 // second queue buffer) must not overlap the binary box or the first buffer
 static_assert(BU8_BYTES <= 2 * QCAP_E * 2 - 320 && QCAP_E * 2 <= 2 * QCAP_E * 2 - 320, "EDT change flags");
+// the wide-window pass's box (tile + 8-pixel halo, int32) fits the layout
+static_assert(E_W + (TS + 16) * (TS + 16) * 4 <= E_BYTES, "EDT wide-window box");
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 // geodesic distance: D as the int32 box layout (stride 72, cell (r, c) at
@@ -1506,6 +1508,192 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
 }
 
 // =====================================================================
+// Distance transform, second wavefront with a wide window (Section 2.2: a
+// sufficiently large neighbourhood makes the propagation exact).  It starts
+// from the fixpoint of the 8-neighbour propagation (the nearest indices the
+// first launch stored) and runs the same update rule with the window of
+// all offsets (dy, dx) with |dy|, |dx| <= k in place of the 8 neighbours:
+// a pixel takes the feature of any window pixel that is strictly closer
+// (equally close with smaller packed coordinates), until no pixel changes.
+// The half-width k of a pixel's window grows with its current squared
+// distance U (KArgs::wide_u[]: k = 1 + the number of the K - 1 thresholds
+// U reaches): the 8-neighbour rule departs from the exact distance only at
+// pixels far from their features (Figure 3), and the farther, the wider
+// the window the correction needs.
+// =====================================================================
+
+template <int K>
+struct Wide {
+    static constexpr int B = TS + 2 * K;  // box side: tile + K-pixel halo
+    static __device__ __forceinline__ int cell(int r, int c) { return r * B + c; }  // box coordinates
+};
+
+// A pixel within k of the tile border changed: the neighbouring tiles whose
+// pixels see it in their windows must be visited again (hdr[H_FLAG..]).
+__device__ __forceinline__ void wide_flag(int *hdr, const JobDesc *jd, int tx, int ty, int ri, int ci, int k) {
+    const int ry0 = ri < k ? 0 : 1, ry1 = ri >= TS - k ? 2 : 1;
+    const int rx0 = ci < k ? 0 : 1, rx1 = ci >= TS - k ? 2 : 1;
+    for (int ry = ry0; ry <= ry1; ++ry)
+        for (int rx = rx0; rx <= rx1; ++rx) {
+            if (ry == 1 && rx == 1) continue;
+            const int ny = ty + ry - 1, nx = tx + rx - 1;
+            if (ny >= 0 && ny < jd->tiles_y && nx >= 0 && nx < jd->tiles_x) hdr[H_FLAG + ry * 3 + rx] = 1;
+        }
+}
+
+template <int NT, int K>
+__device__ bool edt_wide_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, uint32_t &phase,
+                               unsigned long long deadline) {
+    using G = Wide<K>;
+    constexpr int B = G::B;
+    int *hdr = (int *)sm;
+    uint64_t *bar = (uint64_t *)(sm + 256);
+    unsigned *V = (unsigned *)(sm + E_W);  // B x B packed features (the nearest box, converted)
+    const int tid = threadIdx.x;
+    const int lt = gt - jd->tile_base, tx = lt % jd->tiles_x, ty = lt / jd->tiles_x;
+    const int x0 = tx * TS, y0 = ty * TS;
+    const int by = y0 - K, bx = x0 - K;  // global coordinates of box cell (0, 0)
+
+    PhaseClock pc;
+    pc.start();
+    begin_visit(hdr);
+    if (tid == 0) hdr[H_SRC + 4] = ld_acquire(ka.tq.visited + gt);  // 0 on the tile's first visit
+    __syncthreads();
+    // On its first visit a tile holds the 8-neighbour fixpoint, so an inner
+    // pixel (all 8 neighbours in the tile) whose window is the
+    // 8-neighbourhood (k = 1) cannot change in the first pass and is
+    // skipped there; border pixels, later passes and later visits test
+    // every pixel (a neighbour may have changed meanwhile).
+    const bool first = hdr[H_SRC + 4] == 0;
+    // 1. stage the nearest indices of tile + K-pixel halo, then convert them
+    //    to packed coordinates ('inf' outside the image and without feature)
+    if (jd->use_tma) {
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, B * B * 4);
+            tma_load_2d(V, &jd->tm[1], bx, by, bar);
+        }
+        if (!wait_boxes(bar, phase, deadline, ka.ctl)) return false;
+    } else {
+        for (int i = tid; i < B * B; i += NT) {
+            const int r = i / B, c = i - r * B;
+            const int gy = by + r, gx = bx + c;
+            int v = -1;
+            if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) v = __ldcg(jd->nearest + (int64_t)gy * jd->w + gx);
+            V[i] = (unsigned)v;
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < B * B; i += NT) {
+        const int r = i / B, c = i - r * B;
+        const int gy = by + r, gx = bx + c;
+        unsigned v = VR_INF;
+        if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
+            const int idx = (int)V[i];
+            if (idx >= 0) {
+                const int fy = div_w(jd, idx);
+                v = pack_yx(fy, idx - fy * jd->w);
+            }
+        }
+        V[i] = v;
+    }
+    __syncthreads();
+    pc.mark(hdr, 0);
+
+    // 2. window passes until one changes nothing.  Each pixel is written
+    //    only by its own thread; a window cell read while its owner updates
+    //    it gives the old or the new feature, both valid candidates, and a
+    //    pass that changes nothing has compared every pixel with every
+    //    window cell at its final value.
+    bool any = false;
+    int sets = 0;
+    while (true) {
+        bool ch = false;
+        for (int k = tid; k < TS * TS; k += NT) {
+            const int ri = k / TS, ci = k - ri * TS;
+            if (y0 + ri >= jd->h || x0 + ci >= jd->w) continue;
+            const int y = y0 + ri, x = x0 + ci;
+            const int i = G::cell(ri + K, ci + K);
+            const unsigned f = V[i];
+            if (f == pack_yx(y, x)) continue;  // a feature is its own nearest
+            Pick p(f, y, x);
+            const unsigned u = p.dist();
+            int kw = 1;
+#pragma unroll
+            for (int j = 0; j < K - 1; ++j) kw += u >= (unsigned)ka.wide_u[j] ? 1 : 0;
+            if (kw == 1 && first && sets == 0 && ri > 0 && ri < TS - 1 && ci > 0 && ci < TS - 1) continue;
+            unsigned last = VR_INF;
+            for (int dy = -kw; dy <= kw; ++dy) {
+                const unsigned *row = V + i + dy * B;
+                for (int dx = -kw; dx <= kw; ++dx) {
+                    const unsigned g = row[dx];
+                    if (g == last) continue;  // runs of one feature are tested once
+                    last = g;
+                    p.consider(g, y, x);
+                }
+            }
+            const unsigned b = p.best();
+            if (b != f) {
+                V[i] = b;
+                ch = true;
+                wide_flag(hdr, jd, tx, ty, ri, ci, K);
+            }
+        }
+        ++sets;
+        if (!__syncthreads_or(ch)) break;
+        any = true;
+        // a guard only (every pass that changes something improves a pixel,
+        // so the loop ends); thread 0 decides for the whole block
+        if (__syncthreads_or(tid == 0 && globaltimer_ns() > deadline)) {
+            if (tid == 0) {
+                atomicOr(&ka.ctl->status, ST_TIMEOUT);
+                atomicOr(&ka.ctl->sticky, ST_TIMEOUT);
+            }
+            return false;
+        }
+    }
+    if (tid == 0) hdr[H_SETS] = sets;
+    pc.mark(hdr, 1);
+    pc.mark(hdr, 2);
+
+    // 3. store what changed: nearest (linear index) and squared distance
+    if (any) {
+        const bool vec = (jd->w & 3) == 0 && ((reinterpret_cast<uintptr_t>(jd->nearest) |
+                                                reinterpret_cast<uintptr_t>(jd->sqdist)) & 15) == 0;
+        for (int i = tid; i < TS * TS / 4; i += NT) {
+            const int r = i >> 4, q = i & 15;
+            const int gy = y0 + r, gx = x0 + 4 * q;
+            if (gy >= jd->h || gx >= jd->w) continue;
+            int nv[4], dv[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const unsigned f = V[G::cell(r + K, 4 * q + b + K)];
+                nv[b] = f == VR_INF ? -1 : (int)(f >> 16) * jd->w + (int)(f & 0xFFFFu);
+                dv[b] = f == VR_INF ? INT_MAX : (int)d2(gy, gx + b, f);
+            }
+            const int64_t o = (int64_t)gy * jd->w + gx;
+            if (vec && gx + 4 <= jd->w) {
+                *(int4 *)(jd->nearest + o) = make_int4(nv[0], nv[1], nv[2], nv[3]);
+                *(int4 *)(jd->sqdist + o) = make_int4(dv[0], dv[1], dv[2], dv[3]);
+            } else {
+                for (int b = 0; b < 4 && gx + b < jd->w; ++b) {
+                    jd->nearest[o + b] = nv[b];
+                    jd->sqdist[o + b] = dv[b];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && first) {
+        __threadfence();
+        st_release(ka.tq.visited + gt, 1);
+    }
+    finish_tile(ka, jd, gt, tx, ty, hdr);
+    pc.mark(hdr, 3);
+    return true;
+}
+
+// =====================================================================
 // Shortest paths on a grid with obstacles (Section 1's further IWPP use)
 // =====================================================================
 //
@@ -2135,6 +2323,7 @@ __global__ void __launch_bounds__(FAM_NT[FAM], FAM_MINB[FAM]) persistent_kernel(
         } else {
             if constexpr (FAM == FAM_EDT || FAM == FAM_MIXED) {
                 if (jd->op == OP_EDT) ok = edt_visit<NT>(ka, jd, t, smem, phase, deadline);
+                else if (jd->op == OP_EDT_WIDE) ok = edt_wide_visit<NT, 8>(ka, jd, t, smem, phase, deadline);
             }
             if constexpr (FAM == FAM_GDT) {
                 if (jd->op == OP_GDT) ok = gdt_visit<NT>(ka, jd, t, smem, phase, deadline);

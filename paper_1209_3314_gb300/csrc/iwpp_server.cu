@@ -312,7 +312,7 @@ int iwpp_server_submit(iwpp_server *s, const iwpp_request *req, uint64_t *ticket
         if (!r.mask || !r.out || (r.conn != 4 && r.conn != 8) || (r.dtype != IWPP_U8 && r.dtype != IWPP_I32))
             return IWPP_EINVAL;
     } else if (r.op == IWPP_OP_EDT) {
-        if (!r.sqdist || !r.nearest || (r.flags & ~1) || r.h > 32768 || r.w > 32768) return IWPP_EINVAL;
+        if (!r.sqdist || !r.nearest || (r.flags & ~3) || r.h > 32768 || r.w > 32768) return IWPP_EINVAL;
     } else {
         return IWPP_EINVAL;
     }

@@ -123,6 +123,7 @@ def test_autotune_keeps_results(cuda_ctx):
     try:
         best = plan.autotune(reps=2)
         assert 2 <= best["sweeps"] <= 4 and 1 <= best["edt_sweeps"] <= 3
+        assert best["queue_factor"] in (8, 16, 32) and best["spill_cap"] in (1024, 8192)
         for j in jobs:
             if j["op"] == "recon":
                 j["out"].fill_(0)
