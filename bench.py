@@ -573,7 +573,7 @@ def bench_coverage(ctx, dev, d_marker, d_mask, side, reps=3):
             "runs": rows_out}
 
 
-def bench_geodesic(ctx, dev, side, reps=3):
+def bench_geodesic(ctx, dev, side, reps=3, cpu_sample=2048):
     """Shortest paths on a grid with obstacles (iwpp_geodesic): a side x side
     field with 30 % random obstacles and 256 random sources, and a
     serpentine maze of side/8 whose single corridor crosses every tile row
@@ -617,6 +617,19 @@ def bench_geodesic(ctx, dev, side, reps=3):
         ms_ = statistics.median(times)
         res[name] = {"side": int(dm.shape[0]), "ms": round(ms_, 3), "mpx_s": round(dm.numel() / ms_ / 1e3, 1),
                      "tiles_per_call": q["tiles_processed"] // reps}
+        if cpu_sample:
+            # the oracle (Dijkstra's algorithm, one thread) on the same maze,
+            # or on the top-left crop of the field
+            import oracle
+
+            c = min(cpu_sample, mk.shape[0])
+            cm, cs = np.ascontiguousarray(mk[:c, :c]), np.ascontiguousarray(sd[:c, :c])
+            oracle.gdt(cm[:8, :8], cs[:8, :8])
+            t0 = time.perf_counter()
+            oracle.gdt(cm, cs)
+            t = time.perf_counter() - t0
+            res[name]["cpu_oracle"] = {"mpx_s": round(c * c / t / 1e6, 3), "cores": 1,
+                                       "sample": f"top-left {c}x{c}" + (" (the whole maze)" if c == mk.shape[0] else "")}
         del dm, ds, dist
     return res
 
@@ -899,7 +912,7 @@ def run_gpu(args, ws, rank, local):
         coverage = bench_coverage(ctx, dev, d_marker, d_mask, side)
     geodesic = None
     if rank == 0 and not args.skip_geodesic:
-        geodesic = bench_geodesic(ctx, dev, side)
+        geodesic = bench_geodesic(ctx, dev, side, cpu_sample=0 if args.no_cpu_baseline else 2048)
     skiz = None
     if rank == 0 and not args.skip_skiz:
         skiz = bench_skiz(ctx, dev, side, cpu_sample=0 if args.no_cpu_baseline else 2048)

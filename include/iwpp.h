@@ -110,7 +110,9 @@ typedef struct {
     int32_t tile;            /* tile side in pixels: fixed at 64 (0 or 64)    */
     int32_t blocks_per_sm;   /* persistent CTAs per SM, 0 = as many as fit    */
     int32_t sweeps;          /* raster+anti-raster sweep sets per bulk visit   */
-    int32_t queue_factor;    /* tile-queue slots = queue_factor * tiles (>= 1) */
+    int32_t queue_factor;    /* tile-queue slots = queue_factor * tiles (>= 1);
+                                the shortest-path and watershed propagations
+                                (also SKIZ) take 4 * queue_factor            */
     int32_t spill_cap;       /* global spill slots per CTA and buffer (>= 0)   */
     int32_t max_relaunch;    /* device-side relaunches after queue overflow    */
     int32_t timeout_ms;      /* bound on a device-side wait that sees no

@@ -235,6 +235,15 @@ struct Prepared {
     size_t o_slots = 0, o_state = 0, o_visited = 0, o_cnt = 0, o_spill = 0, o_jobs = 0;
 };
 
+// Tile-queue slots per tile of a launch.  The shortest-path and watershed
+// propagations follow paths that bend around obstacles and along optimal
+// edges, so they visit a tile many more times than the reconstruction and
+// the distance transform (6 and more times per tile on random fields, 23 in
+// a 2048^2 serpentine maze): their queues take four times the option.
+int queue_factor_of(int fam, const iwpp_options &opt) {
+    return (fam == FAM_GDT || fam == FAM_WS) ? 4 * opt.queue_factor : opt.queue_factor;
+}
+
 // Byte offsets of a launch's workspace: tile-queue slots, tile states and
 // visited flags, queue counters, per-CTA spill queues, the job table.
 void layout_workspace(Prepared &P, int64_t cap64, size_t njobs, const iwpp_options &opt) {
@@ -255,7 +264,7 @@ int workspace_need(iwpp_ctx *ctx, std::vector<JobDesc> jobs, const iwpp_options 
     Prepared P;
     P.fam = pick_family(jobs);
     P.ntiles = layout_jobs(jobs, TILE);
-    const int64_t cap64 = std::max<int64_t>(P.ntiles + 1, (int64_t)opt.queue_factor * P.ntiles);
+    const int64_t cap64 = std::max<int64_t>(P.ntiles + 1, (int64_t)queue_factor_of(P.fam, opt) * P.ntiles);
     int &occ = ctx->occupancy[P.fam];
     if (occ == 0) CK(family_occupancy(P.fam, &occ), "occupancy query");
     const int bps = opt.blocks_per_sm > 0 ? std::min(opt.blocks_per_sm, occ) : occ;
@@ -278,7 +287,7 @@ int prepare(iwpp_ctx *ctx, std::vector<JobDesc> &jobs, const iwpp_options &opt, 
     for (JobDesc &j : jobs) make_maps(j);
     if (P.ntiles <= 0 || P.ntiles > (int64_t)1 << 28)
         return fail(ctx, IWPP_EINVAL, "tile count %lld out of range", (long long)P.ntiles);
-    const int64_t cap64 = std::max<int64_t>(P.ntiles + 1, (int64_t)opt.queue_factor * P.ntiles);
+    const int64_t cap64 = std::max<int64_t>(P.ntiles + 1, (int64_t)queue_factor_of(P.fam, opt) * P.ntiles);
     if (cap64 > ((int64_t)1 << 31) - 1) return fail(ctx, IWPP_EINVAL, "tile queue too large");
     int &occ = ctx->occupancy[P.fam];
     if (occ == 0) {

@@ -726,43 +726,49 @@ __device__ void recon_border(const JobDesc *jd, const G &g, int *hdr, int x0, in
 }
 
 // Halo cells of neighbour tiles whose J lives in the other buffer (marker
-// vs current result) are read from global memory -- all loads issued before
-// any is used -- then every halo cell is clipped by the mask (halo pixels
-// are sources only, so no later step clips them).
-template <typename T, int NT, typename Cell>
-__device__ __forceinline__ void halo_fixup(const JobDesc *jd, T *J, const T *I, const int *hdr, bool first, int x0,
-                                           int y0, Cell cell) {
-    constexpr int HN = 4 * (TS + 1), HPT = (HN + NT - 1) / NT;
-    const T *mk = (const T *)jd->a;
-    const T *out = (const T *)jd->out;
+// vs current result): fetch() reads them from global memory into registers
+// -- all loads issued before any is used, and before the visit waits for
+// its TMA boxes, so their latency overlaps the copies -- and apply() writes
+// them into the staged J box and clips every halo cell by the mask (halo
+// pixels are sources only, so no later step clips them).
+template <typename T, int NT>
+struct HaloVals {
+    static constexpr int HN = 4 * (TS + 1), HPT = (HN + NT - 1) / NT;
     T val[HPT];
     bool got[HPT];
+    __device__ __forceinline__ void fetch(const JobDesc *jd, const int *hdr, bool first, int x0, int y0) {
+        const T *mk = (const T *)jd->a;
+        const T *out = (const T *)jd->out;
 #pragma unroll
-    for (int u = 0; u < HPT; ++u) {
-        const int k = threadIdx.x + u * NT;
-        got[u] = false;
-        val[u] = 0;
-        if (k >= HN) continue;
-        int r, c;
-        halo_cell(k, r, c);
-        const int src = hdr[H_SRC + region(r) * 3 + region(c)];
-        const int gy = y0 - 1 + r, gx = x0 - 1 + c;
-        if (src != 2 && src != (first ? 0 : 1) && gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
-            val[u] = src == 1 ? __ldcg(out + (int64_t)gy * jd->po + gx) : __ldcg(mk + (int64_t)gy * jd->pa + gx);
-            got[u] = true;
+        for (int u = 0; u < HPT; ++u) {
+            const int k = threadIdx.x + u * NT;
+            got[u] = false;
+            val[u] = 0;
+            if (k >= HN) continue;
+            int r, c;
+            halo_cell(k, r, c);
+            const int src = hdr[H_SRC + region(r) * 3 + region(c)];
+            const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+            if (src != 2 && src != (first ? 0 : 1) && gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
+                val[u] = src == 1 ? __ldcg(out + (int64_t)gy * jd->po + gx) : __ldcg(mk + (int64_t)gy * jd->pa + gx);
+                got[u] = true;
+            }
         }
     }
+    template <typename Cell>
+    __device__ __forceinline__ void apply(T *J, const T *I, Cell cell) {
 #pragma unroll
-    for (int u = 0; u < HPT; ++u) {
-        const int k = threadIdx.x + u * NT;
-        if (k >= HN) continue;
-        int r, c;
-        halo_cell(k, r, c);
-        const int i = cell(r, c);
-        if (got[u]) J[i] = val[u];
-        if (J[i] > I[i]) J[i] = I[i];
+        for (int u = 0; u < HPT; ++u) {
+            const int k = threadIdx.x + u * NT;
+            if (k >= HN) continue;
+            int r, c;
+            halo_cell(k, r, c);
+            const int i = cell(r, c);
+            if (got[u]) J[i] = val[u];
+            if (J[i] > I[i]) J[i] = I[i];
+        }
     }
-}
+};
 
 template <int CONN, int NT>
 __device__ bool recon_u8_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, uint32_t &phase,
@@ -791,7 +797,10 @@ __device__ bool recon_u8_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
     // 1. stage the mask box and the box of the tile's own J source (marker
     //    on a first visit, the current result later); the boxes are the
     //    working layout.  Cells outside the image are zero in J and I (zero
-    //    fill) and so never raise or get raised.
+    //    fill) and so never raise or get raised.  The halo cells that live
+    //    in the other buffer are fetched from global memory while the boxes
+    //    are in flight.
+    HaloVals<uint8_t, NT> hv;
     if (jd->use_tma) {
         if (tid == 0) {
             fence_proxy_async_smem();
@@ -799,16 +808,18 @@ __device__ bool recon_u8_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
             tma_load_2d(IW, &jd->tm[1], x0 - 16, y0 - 1, bar);
             tma_load_2d(JW, &jd->tm[first ? 0 : 2], x0 - 16, y0 - 1, bar);
         }
+        hv.fetch(jd, hdr, first, x0, y0);
         if (!wait_boxes(bar, phase, deadline, ka.ctl)) return false;
     } else {
         stage_plain<uint8_t, BU8_W>(IW, ms, jd->pb, jd->h, jd->w, x0 - 16, y0 - 1, NT);
         stage_plain<uint8_t, BU8_W>(JW, jsrc, jpitch, jd->h, jd->w, x0 - 16, y0 - 1, NT);
+        hv.fetch(jd, hdr, first, x0, y0);
         __syncthreads();
     }
     // halo cells from the other buffer, halo clipped by the mask; the
     // interior is clipped here on a first visit without sweeps (otherwise
     // the first row pass clips every interior pixel)
-    halo_fixup<uint8_t, NT>(jd, JW, IW, hdr, first, x0, y0, U8Grid::cell);
+    hv.apply(JW, IW, U8Grid::cell);
     if (first && ka.sweeps == 0)
         for (int k = tid; k < TS * TS; k += NT) {
             const int i = U8Grid::cell(k / TS + 1, k % TS + 1);
@@ -878,7 +889,9 @@ __device__ bool recon_i32_visit(const KArgs &ka, const JobDesc *jd, int gt, char
 
     // 1. stage the mask box and the box of the tile's own J source (marker
     //    on a first visit, the current result later); the boxes are the
-    //    working layout
+    //    working layout.  The halo cells that live in the other buffer are
+    //    fetched from global memory while the boxes are in flight.
+    HaloVals<int, NT> hv;
     if (jd->use_tma) {
         if (tid == 0) {
             fence_proxy_async_smem();
@@ -886,10 +899,12 @@ __device__ bool recon_i32_visit(const KArgs &ka, const JobDesc *jd, int gt, char
             tma_load_2d(IB, &jd->tm[1], x0 - 4, y0 - 1, bar);
             tma_load_2d(JB, &jd->tm[first ? 0 : 2], x0 - 4, y0 - 1, bar);
         }
+        hv.fetch(jd, hdr, first, x0, y0);
         if (!wait_boxes(bar, phase, deadline, ka.ctl)) return false;
     } else {
         stage_plain<int, BI32_W>(IB, ms, jd->pb, jd->h, jd->w, x0 - 4, y0 - 1, NT);
         stage_plain<int, BI32_W>(JB, jsrc, jpitch, jd->h, jd->w, x0 - 4, y0 - 1, NT);
+        hv.fetch(jd, hdr, first, x0, y0);
         __syncthreads();
     }
     // cells outside the image take the lowest value in J and I, so they
@@ -908,7 +923,7 @@ __device__ bool recon_i32_visit(const KArgs &ka, const JobDesc *jd, int gt, char
     // halo cells from the other buffer, halo clipped by the mask; the
     // interior is clipped here on a first visit without sweeps (otherwise
     // the first row pass clips every interior pixel)
-    halo_fixup<int, NT>(jd, JB, IB, hdr, first, x0, y0, I32Grid::cell);
+    hv.apply(JB, IB, I32Grid::cell);
     if (first && ka.sweeps == 0)
         for (int k = tid; k < TS * TS; k += NT) {
             const int i = I32Grid::cell(k / TS + 1, k % TS + 1);
@@ -1113,7 +1128,9 @@ __device__ __forceinline__ bool edt_row_pass(unsigned *__restrict__ V, int r, in
 // memory, where the neighbouring columns' threads may or may not have
 // stored their new feature yet -- either is a valid candidate, and keeping
 // them off the running feature's dependency chain leaves only the vertical
-// candidate's test on it.
+// candidate's test on it.  The row loop stays rolled: with the two halves
+// of the CTA running the two directions' code at once, a smaller
+// instruction footprint measured 6 % faster than two-fold unrolling.
 template <int DIR>
 __device__ __forceinline__ bool edt_column_pass(unsigned *__restrict__ V, int oy, int ox, int t, uint8_t *RF,
                                                 uint8_t *CF) {
@@ -1132,7 +1149,7 @@ __device__ __forceinline__ bool edt_column_pass(unsigned *__restrict__ V, int oy
         }
     }
     bool ch = false;
-#pragma unroll 2
+#pragma unroll 1
     for (int s = 1; s <= TS; ++s) {
         const int r = DIR > 0 ? s : RR - 1 - s;
         const int i = ecell(r, c), y = oy + r, ip = i - DIR * EP;
@@ -1339,23 +1356,38 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     // 1. VR of tile + halo, converted in place: linear nearest indices of
     //    visited regions -> packed coordinates; unvisited regions from the
     //    binary image (Algorithm 6 initialisation); outside the image 'inf'
-    for (int i = tid; i < RR * EP; i += NT) {
-        const int r = i / EP, c = i - r * EP - 3;
-        if (c < 0 || c >= RR) continue;
-        const int gy = oy + r, gx = ox + c;
-        unsigned v = VR_INF;
-        if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
-            if (hdr[H_SRC + region(r) * 3 + region(c)] == 1) {
-                const int idx = (int)V[i];
-                if (idx >= 0) {
-                    const int fy = div_w(jd, idx);
-                    v = pack_yx(fy, idx - fy * jd->w);
-                }
-            } else if (is_feature(BB[r * BU8_W + c + 15], jd->flags)) {
-                v = pack_yx(gy, gx);
+    if (!need_b && x0 > 0 && y0 > 0 && x0 + TS < jd->w && y0 + TS < jd->h) {
+        // every cell lies in the image and comes from visited regions: a
+        // plain index conversion over the whole box (its padding columns
+        // too), no region lookups
+        for (int i = tid; i < RR * EP; i += NT) {
+            const int idx = (int)V[i];
+            unsigned v = VR_INF;
+            if (idx >= 0) {
+                const int fy = div_w(jd, idx);
+                v = pack_yx(fy, idx - fy * jd->w);
             }
+            V[i] = v;
         }
-        V[i] = v;
+    } else {
+        for (int i = tid; i < RR * EP; i += NT) {
+            const int r = i / EP, c = i - r * EP - 3;
+            if (c < 0 || c >= RR) continue;
+            const int gy = oy + r, gx = ox + c;
+            unsigned v = VR_INF;
+            if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
+                if (hdr[H_SRC + region(r) * 3 + region(c)] == 1) {
+                    const int idx = (int)V[i];
+                    if (idx >= 0) {
+                        const int fy = div_w(jd, idx);
+                        v = pack_yx(fy, idx - fy * jd->w);
+                    }
+                } else if (is_feature(BB[r * BU8_W + c + 15], jd->flags)) {
+                    v = pack_yx(gy, gx);
+                }
+            }
+            V[i] = v;
+        }
     }
     __syncthreads();
     pc.mark(hdr, 0);
@@ -1894,20 +1926,38 @@ __device__ bool gdt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
         if (need_o) stage_plain<int, BI32_W>(D, out, jd->po, jd->h, jd->w, x0 - 4, y0 - 1, NT);
         __syncthreads();
     }
-    for (int i = tid; i < RR * RR; i += NT) {
-        const int r = i / RR, c = i - r * RR;
-        const int gy = y0 - 1 + r, gx = x0 - 1 + c;
-        const int src = hdr[H_SRC + region(r) * 3 + region(c)];
-        int v = GD_INF;
-        if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
-            if (src == 1) {
-                const int o = D[gcell(r, c)];
-                v = o < GD_INF ? o : GD_INF;
-            } else if (M[gmask(r, c)] && __ldg(sd + (int64_t)gy * jd->pb + gx)) {
-                v = 0;
-            }
+    int all_visited = 1;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) all_visited &= hdr[H_SRC + k] == 1;
+    if (all_visited && x0 > 0 && y0 > 0 && x0 + TS < jd->w && y0 + TS < jd->h) {
+        // every cell of the box lies in the image and comes from the
+        // current result: only 'unreachable' (INT32_MAX) maps to GD_INF,
+        // four cells per 16-byte access (the box's padding columns too)
+        int4 *D4 = (int4 *)D;
+        for (int i = tid; i < RR * BI32_W / 4; i += NT) {
+            int4 v = D4[i];
+            v.x = min(v.x, GD_INF);
+            v.y = min(v.y, GD_INF);
+            v.z = min(v.z, GD_INF);
+            v.w = min(v.w, GD_INF);
+            D4[i] = v;
         }
-        D[gcell(r, c)] = v;
+    } else {
+        for (int i = tid; i < RR * RR; i += NT) {
+            const int r = i / RR, c = i - r * RR;
+            const int gy = y0 - 1 + r, gx = x0 - 1 + c;
+            const int src = hdr[H_SRC + region(r) * 3 + region(c)];
+            int v = GD_INF;
+            if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
+                if (src == 1) {
+                    const int o = D[gcell(r, c)];
+                    v = o < GD_INF ? o : GD_INF;
+                } else if (M[gmask(r, c)] && __ldg(sd + (int64_t)gy * jd->pb + gx)) {
+                    v = 0;
+                }
+            }
+            D[gcell(r, c)] = v;
+        }
     }
     __syncthreads();
     pc.mark(hdr, 0);
@@ -1956,14 +2006,26 @@ __device__ bool gdt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
     __syncthreads();
     pc.mark(hdr, 2);
 
-    // 4. store the interior (unreachable: INT32_MAX)
+    // 4. store the interior (unreachable: INT32_MAX), four pixels per
+    //    16-byte store where the TMA maps guarantee 16-byte aligned rows
     load_sources(ka, jd, tx, ty, hdr);
-    for (int i = tid; i < TS * TS; i += NT) {
-        const int r = i / TS, c = i - r * TS;
-        const int gy = y0 + r, gx = x0 + c;
-        if (gy >= jd->h || gx >= jd->w) continue;
-        const int v = D[gcell(r + 1, c + 1)];
-        out[(int64_t)gy * jd->po + gx] = v >= GD_INF ? INT_MAX : v;
+    {
+        const bool vec = jd->use_tma != 0;
+        for (int i = tid; i < TS * TS / 4; i += NT) {
+            const int r = i >> 4, q = i & 15;
+            const int gy = y0 + r, gx = x0 + 4 * q;
+            if (gy >= jd->h || gx >= jd->w) continue;
+            const int4 v4 = *(const int4 *)(D + gcell(r + 1, 4 * q + 1));
+            int vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int b = 0; b < 4; ++b) vv[b] = vv[b] >= GD_INF ? INT_MAX : vv[b];
+            int *dst = out + (int64_t)gy * jd->po + gx;
+            if (vec && gx + 4 <= jd->w) {
+                *(int4 *)dst = make_int4(vv[0], vv[1], vv[2], vv[3]);
+            } else {
+                for (int b = 0; b < 4 && gx + b < jd->w; ++b) dst[b] = vv[b];
+            }
+        }
     }
     __syncthreads();
     publish_tile(ka, gt, hdr);
