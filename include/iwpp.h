@@ -218,14 +218,12 @@ int iwpp_edt_async(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist,
  * definition of Section 2.2, which the propagation method approximates;
  * Figure 3 shows a pixel where it departs), computed by the separable
  * method rather than by propagation.  It runs a column pass (per column,
- * the nearest feature row, in bands of 256 rows) and a row pass: bounded
- * outward searches (256, then 4096 columns each way) settle every pixel
- * whose nearest site provably lies within them; rows with a pixel still
- * unsettled get the exact lower envelope of the parabolas
- * (x - i)^2 + dy_i^2.  All comparisons are
- * exact integer arithmetic.  Same arguments, flags, limits and no-feature
- * convention as iwpp_edt; nearest may be any of several equally near
- * features.  The context workspace grows to 2*h*w*4 bytes plus band
+ * the nearest feature row, in bands of 256 rows) and a row pass that builds
+ * each row's lower envelope of the parabolas (x - i)^2 + dy_i^2, one CTA
+ * per row, so its cost does not depend on the distances.  All comparisons
+ * are exact integer arithmetic.  Same arguments, flags, limits and
+ * no-feature convention as iwpp_edt; nearest may be any of several equally
+ * near features.  The context workspace grows to h*w*4 bytes plus band
  * summaries.  Synchronous: returns after the work on `stream` completed.
  */
 int iwpp_edt_exact(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist,

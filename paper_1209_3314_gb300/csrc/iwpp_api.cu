@@ -963,8 +963,7 @@ int iwpp_edt_exact(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist, int
     const int h = binary->h, w = binary->w, nb = exact_bands(h);
     const size_t band_bytes = align_up((size_t)nb * w * sizeof(int32_t), 256);
     const size_t plane_bytes = align_up((size_t)h * w * sizeof(uint32_t), 256);
-    const size_t flag_bytes = align_up((size_t)h * sizeof(int), 256);
-    if ((rc = ensure_ws(ctx, 4 * band_bytes + 2 * plane_bytes + flag_bytes, st))) return rc;
+    if ((rc = ensure_ws(ctx, 4 * band_bytes + plane_bytes, st))) return rc;
     char *ws = (char *)ctx->ws;
     ExactArgs a;
     a.bin = (const uint8_t *)binary->data;
@@ -978,12 +977,10 @@ int iwpp_edt_exact(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist, int
     a.above = (int32_t *)(ws + 2 * band_bytes);
     a.below = (int32_t *)(ws + 3 * band_bytes);
     a.G = (int32_t *)(ws + 4 * band_bytes);
-    a.stack = (uint32_t *)(ws + 4 * band_bytes + plane_bytes);
-    a.rowflag = (int *)(ws + 4 * band_bytes + 2 * plane_bytes);
     a.sqdist = sqdist;
     a.nearest = nearest;
     CK(launch_edt_exact(a, st), "exact distance transform launch");
-    ctx->launches += 6;
+    ctx->launches += 4;
     ctx->calls += 1;
     CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     return IWPP_OK;

@@ -23,11 +23,6 @@ namespace {
 
 constexpr int XT = 128;  // columns per CTA in the column kernels
 constexpr int BH = 256;  // rows per band in the column pass
-constexpr int SW = 256;   // pixels per row segment in the windowed row passes (threads per CTA)
-constexpr int WB = 256;   // search radius of the first windowed row pass
-constexpr int SR = 8;     // rows per CTA in the first windowed row pass
-constexpr int WB2 = 4096; // search radius of the second windowed row pass
-constexpr int UNSETTLED = -2;  // sqdist marker of a pixel left to the next pass
 
 __device__ __forceinline__ bool feature_px(uint8_t b, int flags) {
     return (flags & 1) ? b != 0 : b == 0;
@@ -104,150 +99,242 @@ __device__ __forceinline__ void cross(uint32_t ea, uint32_t eb, long long &num, 
     den = 2 * (vb - va);
 }
 
-// Outward search from pixel x of row y over the staged column-pass
-// results g (g[i] is column base + i; -1: no site), one column offset d at
-// a time up to radius rad, keeping the nearest site.  Once d^2 is no
-// smaller than the best squared distance found, no site farther out can be
-// nearer, so the pixel is settled exactly; it is also settled when the
-// window covers the whole row.  Returns settled; best / bc / bg describe
-// the nearest site found (bc < 0: none).
-__device__ __forceinline__ bool window_search(const int *g, int base, int x, int y, int w, int rad, long long &best,
-                                              int &bc, int &bg) {
-    best = LLONG_MAX;
-    bc = bg = -1;
-    int d = 0;
-    for (; d <= rad; ++d) {
-        const long long dd = (long long)d * d;
-        if (dd >= best) break;
-        const int gl = g[x - base - d];
-        if (gl >= 0) {
-            const long long c = dd + (long long)(y - gl) * (y - gl);
-            if (c < best) { best = c; bc = x - d; bg = gl; }
+// Row pass geometry: a CTA of ET threads takes one row; thread t owns the
+// chunk of C columns starting at t*C, C = 32 or 64 with ET*C >= w (sides up
+// to 32768).  Chunk t's sites sit at S[t*(C+1) ...] and the owners of its
+// pixels (as positions in S) at own[t*(C+2) ...]: the gaps keep the lanes
+// of a warp on distinct banks when they step through their chunks in
+// lockstep.
+constexpr int ET = 512;
+
+int env_chunk(int w) { return w <= 32 * ET ? 32 : 64; }
+
+size_t env_smem(int w) {
+    const size_t C = env_chunk(w);
+    return ET * (C + 1) * sizeof(uint32_t) + ET * (C + 2) * sizeof(uint16_t) + (4 * ET + 64) * sizeof(int);
+}
+
+// For sites p < q < r (by column): q owns no abscissa once r overtakes q
+// no later than q overtakes p, x(q, r) <= x(p, q).
+__device__ __forceinline__ bool dominated(uint32_t p, uint32_t q, uint32_t r) {
+    long long n1, d1, n2, d2;
+    cross(q, r, n1, d1);
+    cross(p, q, n2, d2);
+    return n1 * d2 <= n2 * d1;
+}
+
+// Merges the envelopes of the chunk groups A = [ca0, cb0) and B = [cb0, cend)
+// (A's columns all left of B's).  Subtracting x^2 turns each parabola into
+// a line whose slope falls with the site's column, so the union's envelope
+// is a prefix of A's followed by a suffix of B's: pop A's last site while
+// the pair (A's second-to-last, B's first) covers it, or B's first while
+// (A's last, B's second) covers it, until neither applies.  Each pop drops
+// a site that owns no abscissa, and at the end both triples across the
+// junction are valid, so the sequence is the union's lower envelope.  lo
+// and hi hold each chunk's live range as positions in S.
+__device__ void merge_envelopes(const uint32_t *S, int *lo, int *hi, int ca0, int cb0, int cend) {
+    int ca = cb0 - 1;
+    while (ca >= ca0 && lo[ca] == hi[ca]) --ca;
+    int cb = cb0;
+    while (cb < cend && lo[cb] == hi[cb]) ++cb;
+    if (ca < ca0 || cb >= cend) return;  // one side empty: nothing to pop
+    // a1: A's last (chunk ca); a0: the one before (chunk cp, pa0 < 0: none)
+    int pa1 = hi[ca] - 1, cp = ca, pa0 = -1;
+    if (pa1 > lo[ca]) pa0 = pa1 - 1;
+    else {
+        for (cp = ca - 1; cp >= ca0 && lo[cp] == hi[cp]; --cp) {}
+        if (cp >= ca0) pa0 = hi[cp] - 1;
+    }
+    // b0: B's first (chunk cb); b1: the one after (chunk cn, pb1 < 0: none)
+    int pb0 = lo[cb], cn = cb, pb1 = -1;
+    if (pb0 + 1 < hi[cb]) pb1 = pb0 + 1;
+    else {
+        for (cn = cb + 1; cn < cend && lo[cn] == hi[cn]; ++cn) {}
+        if (cn < cend) pb1 = lo[cn];
+    }
+    for (;;) {
+        if (pa0 >= 0 && dominated(S[pa0], S[pa1], S[pb0])) {
+            hi[ca] = pa1;  // a1 was the last live entry of chunk ca
+            ca = cp;
+            pa1 = pa0;
+            if (pa1 > lo[ca]) pa0 = pa1 - 1;
+            else {
+                for (cp = ca - 1; cp >= ca0 && lo[cp] == hi[cp]; --cp) {}
+                pa0 = cp >= ca0 ? hi[cp] - 1 : -1;
+            }
+        } else if (pb1 >= 0 && dominated(S[pa1], S[pb0], S[pb1])) {
+            lo[cb] = pb0 + 1;  // b0 was the first live entry of chunk cb
+            cb = cn;
+            pb0 = pb1;
+            if (pb0 + 1 < hi[cb]) pb1 = pb0 + 1;
+            else {
+                for (cn = cb + 1; cn < cend && lo[cn] == hi[cn]; ++cn) {}
+                pb1 = cn < cend ? lo[cn] : -1;
+            }
+        } else {
+            break;
         }
-        if (d > 0) {
-            const int gr = g[x - base + d];
-            if (gr >= 0) {
-                const long long c = dd + (long long)(y - gr) * (y - gr);
-                if (c < best) { best = c; bc = x + d; bg = gr; }
+    }
+}
+
+// The row pass: one CTA per row builds the lower envelope of the row's
+// sites (Felzenszwalb and Huttenlocher's construction, exact rational
+// comparisons) in parallel and colours every pixel of the row with its
+// site.  Its cost does not depend on the distances.
+//  0. The row's column-pass results are staged in chunk layout, eight
+//     loads per thread in flight at a time.
+//  1. Each thread builds its chunk's envelope with the sequential sweep,
+//     in place over the staged entries.
+//  2. log2(ET) rounds merge neighbouring groups of chunks pairwise.
+//  3. The surviving sites, in chunk order, are the row's envelope; each
+//     thread finds the owner of its chunk's first pixel by binary search on
+//     the breakpoints, walks forward across its chunk and records each
+//     pixel's owner; then each warp writes whole chunks, lane by lane.
+__global__ void __launch_bounds__(ET) rows_envelope_kernel(ExactArgs a, int C) {
+    extern __shared__ uint32_t S[];
+    uint16_t *own = (uint16_t *)(S + (size_t)ET * (C + 1));
+    int *lo = (int *)(own + (size_t)ET * (C + 2));
+    int *hi = lo + ET;
+    int *prv = hi + ET;    // the last non-empty chunk at or before c (-1: none)
+    int *nxt = prv + ET;   // the first non-empty chunk at or after c (ET: none)
+    int *wsum = nxt + ET;  // per-warp partial results of the scans
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, w = a.w;
+    const int CO = C + 2, CP = C >> 5;  // CP: 32-column parts per chunk (1 or 2)
+    constexpr int NW = ET / 32, UB = 8;
+    for (int y = blockIdx.x; y < a.h; y += gridDim.x) {
+        __syncthreads();  // shared arrays are reused per row
+        const int32_t *Grow = a.G + (int64_t)y * w;
+        // 0. warp wp stages chunks wp, wp + NW, ...
+        for (int c0 = warp; c0 < ET; c0 += UB * NW) {
+            uint32_t v[UB][2];
+#pragma unroll
+            for (int u = 0; u < UB; ++u)
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const int c = c0 + u * NW, q = c * C + p * 32 + lane;
+                    v[u][p] = (p < CP && c < ET && q < w) ? (uint32_t)__ldg(Grow + q) : 0xFFFFFFFFu;
+                }
+#pragma unroll
+            for (int u = 0; u < UB; ++u)
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const int c = c0 + u * NW;
+                    if (p < CP && c < ET) S[c * (C + 1) + p * 32 + lane] = v[u][p];
+                }
+        }
+        __syncthreads();
+        // 1. the chunk's envelope, written over its own staged entries
+        {
+            uint32_t *my = S + (size_t)tid * (C + 1);
+            const int x0 = tid * C, n = min(C, w - x0);
+            int k = -1;
+            for (int i = 0; i < n; ++i) {
+                const int g = (int)my[i];
+                if (g < 0) continue;
+                const uint32_t e = site_pack(x0 + i, y - g);
+                while (k >= 1 && dominated(my[k - 1], my[k], e)) --k;
+                my[++k] = e;
+            }
+            lo[tid] = tid * (C + 1);
+            hi[tid] = tid * (C + 1) + k + 1;
+        }
+        // 2. pairwise merges
+        for (int span = 1; span < ET; span <<= 1) {
+            __syncthreads();
+            if (tid < ET / (2 * span)) {
+                const int ca0 = tid * 2 * span;
+                merge_envelopes(S, lo, hi, ca0, ca0 + span, ca0 + 2 * span);
             }
         }
-    }
-    // d is the offset the loop stopped at (rad + 1 when it ran out)
-    return (long long)d * d >= best || (x - rad <= 0 && x + rad >= w - 1);
-}
-
-// Stages columns base .. base + n - 1 of G's row y (-1 outside the image).
-__device__ __forceinline__ void stage_row(int *g, const int32_t *Grow, int base, int n, int w) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int c = base + i;
-        g[i] = (c >= 0 && c < w) ? Grow[c] : -1;
-    }
-}
-
-__device__ __forceinline__ void write_site(const ExactArgs &a, int y, int x, long long best, int bc, int bg) {
-    const int64_t o = (int64_t)y * a.w + x;
-    a.sqdist[o] = bc < 0 ? INT_MAX : (int)best;
-    a.nearest[o] = bc < 0 ? -1 : bg * a.w + bc;
-}
-
-// First windowed row pass: a CTA takes SW pixels of SR rows, stages the
-// column-pass results of those columns and WB columns on either side, and
-// searches with radius WB.  A pixel left unsettled is marked in sqdist and
-// flags its row (rowflag 1) for the second pass.
-__global__ void rows_window_kernel(ExactArgs a) {
-    __shared__ int g[SW + 2 * WB];
-    const int x0 = blockIdx.x * SW, x = x0 + threadIdx.x;
-    const int base = x0 - WB;  // column of g[0]
-    for (int rr = 0; rr < SR; ++rr) {
-        const int y = blockIdx.y * SR + rr;
-        if (y >= a.h) break;
         __syncthreads();
-        stage_row(g, a.G + (int64_t)y * a.w, base, SW + 2 * WB, a.w);
+        // 3. the neighbouring non-empty chunks of every chunk (a max scan
+        // and a min scan of the non-empty chunks' indices)
+        const bool live = hi[tid] > lo[tid];
+        int pm = live ? tid : -1, nm = live ? tid : ET;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, pm, d);
+            const int v = __shfl_down_sync(0xffffffffu, nm, d);
+            if (lane >= d) pm = max(pm, u);
+            if (lane + d < 32) nm = min(nm, v);
+        }
+        if (lane == 31) wsum[warp] = pm;
+        if (lane == 0) wsum[32 + warp] = nm;
         __syncthreads();
-        if (x >= a.w) continue;
-        long long best;
-        int bc, bg;
-        if (window_search(g, base, x, y, a.w, WB, best, bc, bg)) {
-            write_site(a, y, x, best, bc, bg);
-        } else {
-            a.sqdist[(int64_t)y * a.w + x] = UNSETTLED;
-            a.rowflag[y] = 1;
+        for (int q = 0; q < ET / 32; ++q) {
+            if (q < warp) pm = max(pm, wsum[q]);
+            if (q > warp) nm = min(nm, wsum[32 + q]);
         }
-    }
-}
-
-// Second windowed row pass, on flagged rows only: radius WB2 for the
-// marked pixels; a pixel still unsettled flags its row (rowflag 2) for the
-// exact envelope pass.
-__global__ void rows_window2_kernel(ExactArgs a) {
-    extern __shared__ int g2[];
-    const int x0 = blockIdx.x * SW, x = x0 + threadIdx.x;
-    const int base = x0 - WB2;
-    for (int rr = 0; rr < SR; ++rr) {
-        const int y = blockIdx.y * SR + rr;
-        if (y >= a.h) break;
-        if (a.rowflag[y] == 0) continue;  // block-uniform
-        const int64_t o = (int64_t)y * a.w + x;
-        const bool mine = x < a.w && a.sqdist[o] == UNSETTLED;
-        if (!__syncthreads_or(mine)) continue;
-        stage_row(g2, a.G + (int64_t)y * a.w, base, SW + 2 * WB2, a.w);
+        prv[tid] = pm;
+        nxt[tid] = nm;
         __syncthreads();
-        if (mine) {
-            long long best;
-            int bc, bg;
-            if (window_search(g2, base, x, y, a.w, WB2, best, bc, bg)) write_site(a, y, x, best, bc, bg);
-            else a.rowflag[y] = 2;
+        int32_t *sq = a.sqdist + (int64_t)y * w;
+        int32_t *nn = a.nearest + (int64_t)y * w;
+        if (prv[ET - 1] < 0) {  // block-uniform: no feature in any column
+            for (int x = tid; x < w; x += ET) {
+                sq[x] = INT_MAX;
+                nn[x] = -1;
+            }
+            continue;
         }
-        __syncthreads();  // g2 is restaged for the next row
-    }
-}
-
-// One thread per row: the lower envelope of the row's sites (Felzenszwalb
-// and Huttenlocher's sweep, with exact rational comparisons), then the
-// nearest site of every pixel.  Runs on the rows the windowed passes left
-// unsettled (rowflag 2).
-__global__ void rows_kernel(ExactArgs a) {
-    const int y = blockIdx.x * blockDim.x + threadIdx.x;
-    if (y >= a.h || a.rowflag[y] != 2) return;
-    const int w = a.w;
-    const int32_t *Grow = a.G + (int64_t)y * w;
-    uint32_t *S = a.stack + (int64_t)y * w;
-    int k = -1;
-    for (int q = 0; q < w; ++q) {
-        const int g = Grow[q];
-        if (g < 0) continue;
-        const uint32_t e = site_pack(q, y - g);
-        // pop the top while the new site's parabola overtakes it no later
-        // than the top overtook the entry below it
-        while (k >= 1) {
-            long long n1, d1, n2, d2;
-            cross(S[k], e, n1, d1);
-            cross(S[k - 1], S[k], n2, d2);
-            if (n1 * d2 <= n2 * d1) --k;
-            else break;
-        }
-        S[++k] = e;
-    }
-    int32_t *sq = a.sqdist + (int64_t)y * w;
-    int32_t *nn = a.nearest + (int64_t)y * w;
-    if (k < 0) {
-        for (int x = 0; x < w; ++x) {
-            sq[x] = INT_MAX;
-            nn[x] = -1;
-        }
-        return;
-    }
-    int j = 0;
-    for (int x = 0; x < w; ++x) {
-        while (j < k) {
+        // bp(p, q) <= x: from x on, the envelope's site at q is at least as
+        // near as its predecessor at p
+        auto reached = [&](int p, int q, int x) {
             long long n, d;
-            cross(S[j], S[j + 1], n, d);
-            if (n <= (long long)x * d) ++j;  // the next site is at least as near from x on
-            else break;
+            cross(S[p], S[q], n, d);
+            return n <= (long long)x * d;
+        };
+        // the first site of non-empty chunk c owns an abscissa <= x
+        auto starts_by = [&](int c, int x) {
+            const int pc = c > 0 ? prv[c - 1] : -1;
+            return pc < 0 || reached(hi[pc] - 1, lo[c], x);
+        };
+        const int x0 = tid * C, x1 = min(w, x0 + C);
+        if (x0 < w) {
+            // the owner of x0: in the last non-empty chunk whose first site
+            // starts by x0 (breakpoints increase along the envelope; the
+            // first non-empty chunk always qualifies), ...
+            int l = nxt[0], r = ET - 1;
+            while (l < r) {
+                const int m = (l + r + 1) >> 1;
+                if (starts_by(prv[m], x0)) l = m;
+                else r = m - 1;
+            }
+            int c = prv[l];
+            // ... at its last site that starts by x0
+            int pl = lo[c], pr = hi[c] - 1;
+            while (pl < pr) {
+                const int m = (pl + pr + 1) >> 1;
+                if (reached(m - 1, m, x0)) pl = m;
+                else pr = m - 1;
+            }
+            int pos = pl;
+            auto succ = [&](int p, int &cc) {
+                if (p + 1 < hi[cc]) return p + 1;
+                const int n2 = cc + 1 < ET ? nxt[cc + 1] : ET;
+                if (n2 >= ET) return -1;
+                cc = n2;
+                return lo[n2];
+            };
+            int cn = c, nx = succ(pos, cn);
+            for (int x = x0; x < x1; ++x) {
+                while (nx >= 0 && reached(pos, nx, x)) {
+                    pos = nx;
+                    c = cn;
+                    nx = succ(pos, cn);
+                }
+                own[tid * CO + (x - x0)] = (uint16_t)pos;
+            }
         }
-        const int v = site_v(S[j]), dy = site_dy(S[j]);
-        sq[x] = (x - v) * (x - v) + dy * dy;
-        nn[x] = (y - dy) * w + v;
+        __syncthreads();
+        for (int c = warp; c < ET; c += ET / 32)
+            for (int k = lane; k < C; k += 32) {
+                const int x = c * C + k;
+                if (x >= w) break;
+                const uint32_t e = S[own[c * CO + k]];
+                const int v = site_v(e), dy = site_dy(e);
+                sq[x] = (x - v) * (x - v) + dy * dy;
+                nn[x] = (y - dy) * w + v;
+            }
     }
 }
 
@@ -258,17 +345,14 @@ int exact_bands(int h) { return (h + BH - 1) / BH; }
 cudaError_t launch_edt_exact(const ExactArgs &a, cudaStream_t s) {
     cudaGetLastError();
     const dim3 gx((a.w + XT - 1) / XT), gxb((a.w + XT - 1) / XT, a.nb);
-    cudaError_t e = cudaMemsetAsync(a.rowflag, 0, (size_t)a.h * sizeof(int), s);
-    if (e != cudaSuccess) return e;
     band_ends_kernel<<<gxb, XT, 0, s>>>(a);
     band_links_kernel<<<gx, XT, 0, s>>>(a);
     columns_kernel<<<gxb, XT, 0, s>>>(a);
-    rows_window_kernel<<<dim3((a.w + SW - 1) / SW, (a.h + SR - 1) / SR), SW, 0, s>>>(a);
-    const int smem2 = (SW + 2 * WB2) * (int)sizeof(int);
-    e = cudaFuncSetAttribute(rows_window2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
+    const int C = env_chunk(a.w);
+    const int smem = (int)env_smem(a.w);
+    cudaError_t e = cudaFuncSetAttribute(rows_envelope_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    rows_window2_kernel<<<dim3((a.w + SW - 1) / SW, (a.h + SR - 1) / SR), SW, smem2, s>>>(a);
-    rows_kernel<<<(a.h + 31) / 32, 32, 0, s>>>(a);
+    rows_envelope_kernel<<<min(a.h, 1024), ET, smem, s>>>(a, C);
     return cudaGetLastError();
 }
 

@@ -85,8 +85,6 @@ struct ExactArgs {
     int h, w, flags, nb;  // nb: bands of the column pass
     int32_t *first, *last, *above, *below;  // nb x w band summaries
     int32_t *G;           // h x w scratch: row of the nearest feature in the pixel's column
-    uint32_t *stack;      // h x w scratch: the envelope stacks of the fallback row pass
-    int *rowflag;         // h: row has a pixel the windowed search could not settle
     int32_t *sqdist, *nearest;
 };
 int exact_bands(int h);

@@ -85,6 +85,40 @@ def test_never_above_propagation_and_equal_off_departures(cuda_ctx):
     assert (sq_p != sq_e).mean() < 1e-3
 
 
+@pytest.mark.parametrize("fnz", [False, True])
+def test_far_pixels_and_envelope_shapes(cuda_ctx, fnz):
+    """Rows whose pixels lie thousands of columns from every site of the
+    row: one feature in a corner (one site per row), a few scattered ones,
+    a feature row far off (all sites equally far: every site is on the
+    envelope), and a row band where the sites' distances vary along the
+    row, with a 9000-column gap."""
+    rng = np.random.default_rng(31 + fnz)
+    cases = []
+    b = np.zeros((600, 20000), np.uint8)
+    b[599, 0] = 1
+    cases.append(b)
+    b = np.zeros((2000, 12000), np.uint8)
+    for y, x in zip(rng.integers(0, 2000, 4), rng.integers(0, 12000, 4)):
+        b[y, x] = 1
+    cases.append(b)
+    b = np.zeros((4400, 9001), np.uint8)
+    b[0, :] = 1  # every column has a site; all at the same row offset
+    cases.append(b)
+    b = np.zeros((257, 16384), np.uint8)
+    xs = np.arange(16384)
+    ys = (128 + 120 * np.sin(xs / 900.0)).astype(int)
+    keep = rng.random(16384) < 0.3
+    b[ys[keep], xs[keep]] = 1
+    b[:, 5000:14000] = 0  # a wide gap with no site
+    cases.append(b)
+    for b in cases:
+        if not fnz:
+            b = (1 - b).astype(np.uint8)  # features are the 0 pixels
+        sq, nn = run(cuda_ctx, b, fnz)
+        np.testing.assert_array_equal(sq, oracle.edt_exact(b, fnz))
+        check_nearest(b, sq, nn, fnz, sample=200_000)
+
+
 def test_largest_side_and_invalid(cuda_ctx):
     for shape in ((1, 32768), (32768, 1), (3, 32768)):
         rng = np.random.default_rng(sum(shape) + 1)
