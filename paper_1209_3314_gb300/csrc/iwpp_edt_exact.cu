@@ -123,21 +123,9 @@ __device__ __forceinline__ bool dominated(uint32_t p, uint32_t q, uint32_t r) {
     return n1 * d2 <= n2 * d1;
 }
 
-// Merges the envelopes of the chunk groups A = [ca0, cb0) and B = [cb0, cend)
-// (A's columns all left of B's).  Subtracting x^2 turns each parabola into
-// a line whose slope falls with the site's column, so the union's envelope
-// is a prefix of A's followed by a suffix of B's: pop A's last site while
-// the pair (A's second-to-last, B's first) covers it, or B's first while
-// (A's last, B's second) covers it, until neither applies.  Each pop drops
-// a site that owns no abscissa, and at the end both triples across the
-// junction are valid, so the sequence is the union's lower envelope.  lo
-// and hi hold each chunk's live range as positions in S.
-__device__ void merge_envelopes(const uint32_t *S, int *lo, int *hi, int ca0, int cb0, int cend) {
-    int ca = cb0 - 1;
-    while (ca >= ca0 && lo[ca] == hi[ca]) --ca;
-    int cb = cb0;
-    while (cb < cend && lo[cb] == hi[cb]) ++cb;
-    if (ca < ca0 || cb >= cend) return;  // one side empty: nothing to pop
+// The pops of merge_envelopes (below), from A's last non-empty chunk ca and
+// B's first cb; A spans chunks ca0 .. ca, B chunks cb .. cend - 1.
+__device__ __forceinline__ void merge_sides(const uint32_t *S, int *lo, int *hi, int ca0, int ca, int cb, int cend) {
     // a1: A's last (chunk ca); a0: the one before (chunk cp, pa0 < 0: none)
     int pa1 = hi[ca] - 1, cp = ca, pa0 = -1;
     if (pa1 > lo[ca]) pa0 = pa1 - 1;
@@ -175,6 +163,28 @@ __device__ void merge_envelopes(const uint32_t *S, int *lo, int *hi, int ca0, in
             break;
         }
     }
+}
+
+// Merges the envelopes of the chunk groups A = [ca0, cb0) and B = [cb0, cend)
+// (A's columns all left of B's).  Subtracting x^2 turns each parabola into
+// a line whose slope falls with the site's column, so the union's envelope
+// is a prefix of A's followed by a suffix of B's: pop A's last site while
+// the pair (A's second-to-last, B's first) covers it, or B's first while
+// (A's last, B's second) covers it, until neither applies.  Each pop drops
+// a site that owns no abscissa, and at the end both triples across the
+// junction are valid, so the sequence is the union's lower envelope.  lo
+// and hi hold each chunk's live range as positions in S; gf / gl, indexed
+// by a group's first chunk, its first / last non-empty chunk (-1: none).
+// A group's first site and its last are never popped (each is the only
+// site that owns the abscissae far enough to its side), so gf and gl of
+// the merged group follow from the two groups'.
+__device__ __forceinline__ void merge_envelopes(const uint32_t *S, int *lo, int *hi, int *gf, int *gl, int ca0, int cb0,
+                                int cend) {
+    const int ca = gl[ca0], cb = gf[cb0];
+    gf[ca0] = ca >= 0 ? gf[ca0] : cb;
+    gl[ca0] = cb >= 0 ? gl[cb0] : ca;
+    if (ca < 0 || cb < 0) return;  // one side empty: nothing to pop
+    merge_sides(S, lo, hi, ca0, ca, cb, cend);
 }
 
 // The row pass: one CTA per row builds the lower envelope of the row's
@@ -237,13 +247,14 @@ __global__ void __launch_bounds__(ET) rows_envelope_kernel(ExactArgs a, int C) {
             }
             lo[tid] = tid * (C + 1);
             hi[tid] = tid * (C + 1) + k + 1;
+            prv[tid] = nxt[tid] = k >= 0 ? tid : -1;  // the chunk's group: its first / last non-empty chunk
         }
         // 2. pairwise merges
         for (int span = 1; span < ET; span <<= 1) {
             __syncthreads();
             if (tid < ET / (2 * span)) {
                 const int ca0 = tid * 2 * span;
-                merge_envelopes(S, lo, hi, ca0, ca0 + span, ca0 + 2 * span);
+                merge_envelopes(S, lo, hi, prv, nxt, ca0, ca0 + span, ca0 + 2 * span);
             }
         }
         __syncthreads();
@@ -307,28 +318,31 @@ __global__ void __launch_bounds__(ET) rows_envelope_kernel(ExactArgs a, int C) {
                 if (reached(m - 1, m, x0)) pl = m;
                 else pr = m - 1;
             }
-            int pos = pl;
-            auto succ = [&](int p, int &cc) {
-                if (p + 1 < hi[cc]) return p + 1;
-                const int n2 = cc + 1 < ET ? nxt[cc + 1] : ET;
-                if (n2 >= ET) return -1;
-                cc = n2;
-                return lo[n2];
+            // the site after pos (chunk c): nx in chunk cn, nx < 0: none
+            int pos = pl, cn = c, nx = -1;
+            auto advance_next = [&]() {
+                if (pos + 1 < hi[c]) {
+                    cn = c;
+                    nx = pos + 1;
+                } else {
+                    cn = c + 1 < ET ? nxt[c + 1] : ET;
+                    nx = cn < ET ? lo[cn] : -1;
+                }
             };
-            int cn = c, nx = succ(pos, cn);
+            advance_next();
             for (int x = x0; x < x1; ++x) {
                 while (nx >= 0 && reached(pos, nx, x)) {
                     pos = nx;
                     c = cn;
-                    nx = succ(pos, cn);
+                    advance_next();
                 }
                 own[tid * CO + (x - x0)] = (uint16_t)pos;
             }
         }
         __syncthreads();
-        for (int c = warp; c < ET; c += ET / 32)
-            for (int k = lane; k < C; k += 32) {
-                const int x = c * C + k;
+        for (int c = warp; c < ET; c += NW)
+            for (int p = 0; p < CP; ++p) {
+                const int k = p * 32 + lane, x = c * C + k;
                 if (x >= w) break;
                 const uint32_t e = S[own[c * CO + k]];
                 const int v = site_v(e), dy = site_dy(e);
@@ -352,7 +366,13 @@ cudaError_t launch_edt_exact(const ExactArgs &a, cudaStream_t s) {
     const int smem = (int)env_smem(a.w);
     cudaError_t e = cudaFuncSetAttribute(rows_envelope_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    rows_envelope_kernel<<<min(a.h, 1024), ET, smem, s>>>(a, C);
+    // one wave of resident CTAs, each taking rows blockIdx.x + k * grid
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_envelope_kernel, ET, smem)) != cudaSuccess)
+        return e;
+    rows_envelope_kernel<<<min(a.h, max(1, sms * per_sm)), ET, smem, s>>>(a, C);
     return cudaGetLastError();
 }
 
