@@ -218,7 +218,7 @@ int iwpp_edt_async(iwpp_ctx *ctx, const iwpp_image *binary, int32_t *sqdist,
  * definition of Section 2.2, which the propagation method approximates;
  * Figure 3 shows a pixel where it departs), computed by the separable
  * method rather than by propagation.  It runs a column pass (per column,
- * the nearest feature row, in bands of 256 rows) and a row pass that builds
+ * the nearest feature row, in bands of 128 rows) and a row pass that builds
  * each row's lower envelope of the parabolas (x - i)^2 + dy_i^2, one CTA
  * per row, so its cost does not depend on the distances.  All comparisons
  * are exact integer arithmetic.  Same arguments, flags, limits and

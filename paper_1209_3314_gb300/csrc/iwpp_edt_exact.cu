@@ -22,7 +22,7 @@ namespace iwpp {
 namespace {
 
 constexpr int XT = 128;  // columns per CTA in the column kernels
-constexpr int BH = 256;  // rows per band in the column pass
+constexpr int BH = 128;  // rows per band in the column pass
 
 __device__ __forceinline__ bool feature_px(uint8_t b, int flags) {
     return (flags & 1) ? b != 0 : b == 0;
@@ -65,21 +65,23 @@ __global__ void band_links_kernel(ExactArgs a) {
 
 // Per (column, band): the row of the nearest feature in the pixel's column
 // (-1: the column has none), written to G.  Downward pass: the last
-// feature at or above; upward pass: the first at or below; the nearer wins
-// (the upper one on a tie).
+// feature at or above, kept in shared memory (16 bits: rows < 32768);
+// upward pass: the first at or below; the nearer wins (the upper one on a
+// tie), and G is written once.
 __global__ void columns_kernel(ExactArgs a) {
+    __shared__ int16_t U[BH][XT];
     const int x = blockIdx.x * XT + threadIdx.x, b = blockIdx.y;
-    if (x >= a.w) return;
+    if (x >= a.w) return;  // no barrier below: each thread keeps to its own column of U
     const int r0 = b * BH, r1 = min(a.h, r0 + BH);
     int up = a.above[(int64_t)b * a.w + x];
     for (int r = r0; r < r1; ++r) {
         if (feature_px(__ldg(a.bin + (int64_t)r * a.pitch + x), a.flags)) up = r;
-        a.G[(int64_t)r * a.w + x] = up;
+        U[r - r0][threadIdx.x] = (int16_t)up;
     }
     int dn = a.below[(int64_t)b * a.w + x];
     for (int r = r1 - 1; r >= r0; --r) {
         if (feature_px(__ldg(a.bin + (int64_t)r * a.pitch + x), a.flags)) dn = r;
-        const int u = a.G[(int64_t)r * a.w + x];
+        const int u = U[r - r0][threadIdx.x];
         a.G[(int64_t)r * a.w + x] = (u >= 0 && (dn < 0 || r - u <= dn - r)) ? u : dn;
     }
 }
@@ -191,15 +193,15 @@ __device__ __forceinline__ void merge_envelopes(const uint32_t *S, int *lo, int 
 // sites (Felzenszwalb and Huttenlocher's construction, exact rational
 // comparisons) in parallel and colours every pixel of the row with its
 // site.  Its cost does not depend on the distances.
-//  0. The row's column-pass results are staged in chunk layout, eight
-//     loads per thread in flight at a time.
+//  0. The row's column-pass results are staged in chunk layout, each
+//     warp its own lanes' chunks, eight loads per thread in flight.
 //  1. Each thread builds its chunk's envelope with the sequential sweep,
 //     in place over the staged entries.
 //  2. log2(ET) rounds merge neighbouring groups of chunks pairwise.
 //  3. The surviving sites, in chunk order, are the row's envelope; each
 //     thread finds the owner of its chunk's first pixel by binary search on
 //     the breakpoints, walks forward across its chunk and records each
-//     pixel's owner; then each warp writes whole chunks, lane by lane.
+//     pixel's owner; then each warp writes its lanes' chunks, coalesced.
 __global__ void __launch_bounds__(ET) rows_envelope_kernel(ExactArgs a, int C) {
     extern __shared__ uint32_t S[];
     uint16_t *own = (uint16_t *)(S + (size_t)ET * (C + 1));
@@ -210,29 +212,30 @@ __global__ void __launch_bounds__(ET) rows_envelope_kernel(ExactArgs a, int C) {
     int *wsum = nxt + ET;  // per-warp partial results of the scans
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, w = a.w;
     const int CO = C + 2, CP = C >> 5;  // CP: 32-column parts per chunk (1 or 2)
-    constexpr int NW = ET / 32, UB = 8;
+    constexpr int UB = 8;
     for (int y = blockIdx.x; y < a.h; y += gridDim.x) {
         __syncthreads();  // shared arrays are reused per row
         const int32_t *Grow = a.G + (int64_t)y * w;
-        // 0. warp wp stages chunks wp, wp + NW, ...
-        for (int c0 = warp; c0 < ET; c0 += UB * NW) {
+        // 0. each warp stages its own 32 chunks (its lanes' chunks), so the
+        // phases up to the wide merges need only warp barriers
+        for (int u0 = 0; u0 < 32; u0 += UB) {
             uint32_t v[UB][2];
 #pragma unroll
             for (int u = 0; u < UB; ++u)
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
-                    const int c = c0 + u * NW, q = c * C + p * 32 + lane;
-                    v[u][p] = (p < CP && c < ET && q < w) ? (uint32_t)__ldg(Grow + q) : 0xFFFFFFFFu;
+                    const int c = warp * 32 + u0 + u, q = c * C + p * 32 + lane;
+                    v[u][p] = (p < CP && q < w) ? (uint32_t)__ldg(Grow + q) : 0xFFFFFFFFu;
                 }
 #pragma unroll
             for (int u = 0; u < UB; ++u)
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
-                    const int c = c0 + u * NW;
-                    if (p < CP && c < ET) S[c * (C + 1) + p * 32 + lane] = v[u][p];
+                    const int c = warp * 32 + u0 + u;
+                    if (p < CP) S[c * (C + 1) + p * 32 + lane] = v[u][p];
                 }
         }
-        __syncthreads();
+        __syncwarp();
         // 1. the chunk's envelope, written over its own staged entries
         {
             uint32_t *my = S + (size_t)tid * (C + 1);
@@ -249,13 +252,13 @@ __global__ void __launch_bounds__(ET) rows_envelope_kernel(ExactArgs a, int C) {
             hi[tid] = tid * (C + 1) + k + 1;
             prv[tid] = nxt[tid] = k >= 0 ? tid : -1;  // the chunk's group: its first / last non-empty chunk
         }
-        // 2. pairwise merges
+        // 2. pairwise merges, each by the thread of the group's first chunk:
+        // up to groups of 32 chunks, a merge reads only what lanes of its
+        // own warp wrote, so a warp barrier orders the rounds
         for (int span = 1; span < ET; span <<= 1) {
-            __syncthreads();
-            if (tid < ET / (2 * span)) {
-                const int ca0 = tid * 2 * span;
-                merge_envelopes(S, lo, hi, prv, nxt, ca0, ca0 + span, ca0 + 2 * span);
-            }
+            if (span < 32) __syncwarp();
+            else __syncthreads();
+            if ((tid & (2 * span - 1)) == 0) merge_envelopes(S, lo, hi, prv, nxt, tid, tid + span, tid + 2 * span);
         }
         __syncthreads();
         // 3. the neighbouring non-empty chunks of every chunk (a max scan
@@ -339,8 +342,8 @@ __global__ void __launch_bounds__(ET) rows_envelope_kernel(ExactArgs a, int C) {
                 own[tid * CO + (x - x0)] = (uint16_t)pos;
             }
         }
-        __syncthreads();
-        for (int c = warp; c < ET; c += NW)
+        __syncwarp();  // each warp writes out its own lanes' chunks
+        for (int c = warp * 32; c < warp * 32 + 32; ++c)
             for (int p = 0; p < CP; ++p) {
                 const int k = p * 32 + lane, x = c * C + k;
                 if (x >= w) break;
