@@ -205,6 +205,40 @@ def issue_roofline(kernel_key, side, ms, sm_mhz):
             "peak_source": "152 SMs x 4 schedulers x 1 warp instruction per cycle x sampled median SM clock"}
 
 
+def host_link(dev, n=1 << 30):
+    """Pinned host<->device copy rates of this machine (GB/s, best of 3): each
+    direction alone and both at once on two streams.  The end-to-end step
+    cannot beat its bytes over these rates."""
+    import torch
+
+    hs = [torch.empty(n, dtype=torch.uint8).pin_memory() for _ in range(2)]
+    ds = [torch.empty(n, dtype=torch.uint8, device=dev) for _ in range(2)]
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def best(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        b = 1e30
+        for _ in range(3):
+            t = time.perf_counter()
+            fn()
+            torch.cuda.synchronize(dev)
+            b = min(b, time.perf_counter() - t)
+        return b
+
+    def both():
+        with torch.cuda.stream(s1):
+            ds[0].copy_(hs[0], non_blocking=True)
+        with torch.cuda.stream(s2):
+            hs[1].copy_(ds[1], non_blocking=True)
+
+    res = {"h2d": round(n / best(lambda: ds[0].copy_(hs[0], non_blocking=True)) / 1e9, 1),
+           "d2h": round(n / best(lambda: hs[1].copy_(ds[1], non_blocking=True)) / 1e9, 1),
+           "both_ways": round(2 * n / best(both) / 1e9, 1)}
+    del hs, ds
+    return res
+
+
 def host_cpu():
     """CPU model and the number of host cores this process may use."""
     model = ""
@@ -853,6 +887,7 @@ def run_gpu(args, ws, rank, local):
     # (context, stream, device buffers, pinned result buffers) take steps
     # in turn, so one step's host<->device copies overlap the other's
     # kernels; every step still copies its inputs in and its results out.
+    link = host_link(dev)
     h_marker = torch.from_numpy(marker).pin_memory()
     h_mask = torch.from_numpy(mask).pin_memory()
     h_bin = torch.from_numpy(binary).pin_memory()
@@ -1012,7 +1047,10 @@ def run_gpu(args, ws, rank, local):
             "watershed": watershed,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_val, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3), "check": ok},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3), "check": ok,
+                    "host_link_gbs": link,
+                    "link_bound_ms": round(max(h2d / link["h2d"], d2h / link["d2h"],
+                                               (h2d + d2h) / link["both_ways"]) / 1e6, 3)},
             "clocks": clocks,
             "gpu_launches": launches,
         }

@@ -475,7 +475,7 @@ int iwpp_stats_reset(iwpp_ctx *ctx);
  *     calls whose GPU work overlaps (different streams or threads on one
  *     device) race -- serialise them;
  *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make it before any stream capture;
+ *     (cudaGetSymbolAddress);
  *   - a device-side wait gives up after 10 s without progress.
  * Returns IWPP_OK, IWPP_EINVAL, IWPP_ECUDA, IWPP_ETIMEOUT or IWPP_EOVERFLOW.
  */

@@ -21,7 +21,7 @@
 //     threads on one device) race and corrupt each other's results -- order
 //     them on one stream;
 //   * the first call on a device resolves the array's device address with
-//     cudaGetSymbolAddress; make that first call before any stream capture;
+//     cudaGetSymbolAddress;
 //   * images larger than the array supports are rejected with IWPP_EINVAL
 //     (no more than IWPP_NOALLOC_MAX_TILES tiles of 64x64 pixels);
 //   * the call is synchronous: it returns after the work on `stream` has
