@@ -1360,33 +1360,56 @@ __device__ bool edt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
         // every cell lies in the image and comes from visited regions: a
         // plain index conversion over the whole box (its padding columns
         // too), no region lookups
-        for (int i = tid; i < RR * EP; i += NT) {
-            const int idx = (int)V[i];
-            unsigned v = VR_INF;
-            if (idx >= 0) {
-                const int fy = div_w(jd, idx);
-                v = pack_yx(fy, idx - fy * jd->w);
-            }
-            V[i] = v;
-        }
-    } else {
-        for (int i = tid; i < RR * EP; i += NT) {
-            const int r = i / EP, c = i - r * EP - 3;
-            if (c < 0 || c >= RR) continue;
-            const int gy = oy + r, gx = ox + c;
-            unsigned v = VR_INF;
-            if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
-                if (hdr[H_SRC + region(r) * 3 + region(c)] == 1) {
-                    const int idx = (int)V[i];
-                    if (idx >= 0) {
-                        const int fy = div_w(jd, idx);
-                        v = pack_yx(fy, idx - fy * jd->w);
-                    }
-                } else if (is_feature(BB[r * BU8_W + c + 15], jd->flags)) {
-                    v = pack_yx(gy, gx);
+        uint4 *V4 = (uint4 *)V;
+        for (int i = tid; i < RR * EP / 4; i += NT) {
+            const uint4 w4 = V4[i];
+            unsigned v[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int idx = (int)v[b];
+                v[b] = VR_INF;
+                if (idx >= 0) {
+                    const int fy = div_w(jd, idx);
+                    v[b] = pack_yx(fy, idx - fy * jd->w);
                 }
             }
-            V[i] = v;
+            V4[i] = make_uint4(v[0], v[1], v[2], v[3]);
+        }
+    } else {
+        // four cells per step: words 4q .. 4q+3 of a row hold cells
+        // 4q-3 .. 4q, which lie in one column region (q = 0: the left halo
+        // and padding; q = 17: the right halo and padding; else interior),
+        // and their binary bytes are one aligned 32-bit word of the box
+        for (int g = tid; g < RR * (EP / 4); g += NT) {
+            const int r = g / (EP / 4), q = g - r * (EP / 4);
+            const int gy = oy + r, c0 = 4 * q - 3;
+            const int src = hdr[H_SRC + region(r) * 3 + (q == 0 ? 0 : (q == EP / 4 - 1 ? 2 : 1))];
+            uint4 *vp = (uint4 *)(V + r * EP + 4 * q);
+            unsigned v[4] = {VR_INF, VR_INF, VR_INF, VR_INF};
+            if (gy >= 0 && gy < jd->h) {
+                if (src == 1) {
+                    const uint4 w4 = *vp;
+                    const int idx[4] = {(int)w4.x, (int)w4.y, (int)w4.z, (int)w4.w};
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int c = c0 + b, gx = ox + c;
+                        if (c >= 0 && c < RR && gx >= 0 && gx < jd->w && idx[b] >= 0) {
+                            const int fy = div_w(jd, idx[b]);
+                            v[b] = pack_yx(fy, idx[b] - fy * jd->w);
+                        }
+                    }
+                } else {
+                    const unsigned bw = *(const unsigned *)(BB + r * BU8_W + 4 * q + 12);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int c = c0 + b, gx = ox + c;
+                        if (c >= 0 && c < RR && gx >= 0 && gx < jd->w &&
+                            is_feature((uint8_t)(bw >> (8 * b)), jd->flags))
+                            v[b] = pack_yx(gy, gx);
+                    }
+                }
+            }
+            *vp = make_uint4(v[0], v[1], v[2], v[3]);
         }
     }
     __syncthreads();
@@ -1943,20 +1966,40 @@ __device__ bool gdt_visit(const KArgs &ka, const JobDesc *jd, int gt, char *sm, 
             D4[i] = v;
         }
     } else {
-        for (int i = tid; i < RR * RR; i += NT) {
-            const int r = i / RR, c = i - r * RR;
-            const int gy = y0 - 1 + r, gx = x0 - 1 + c;
-            const int src = hdr[H_SRC + region(r) * 3 + region(c)];
-            int v = GD_INF;
-            if (gy >= 0 && gy < jd->h && gx >= 0 && gx < jd->w) {
+        // four cells per step: words 4q .. 4q+3 of a row hold cells
+        // 4q-3 .. 4q, which lie in one column region, and their mask bytes
+        // are one aligned 32-bit word of the mask box; the sources' bytes
+        // are read from global memory, all four loads in flight at once
+        for (int g = tid; g < RR * (BI32_W / 4); g += NT) {
+            const int r = g / (BI32_W / 4), q = g - r * (BI32_W / 4);
+            const int gy = y0 - 1 + r, c0 = 4 * q - 3;
+            const int src = hdr[H_SRC + region(r) * 3 + (q == 0 ? 0 : (q == BI32_W / 4 - 1 ? 2 : 1))];
+            int4 *dp = (int4 *)(D + r * BI32_W + 4 * q);
+            int v[4] = {GD_INF, GD_INF, GD_INF, GD_INF};
+            if (gy >= 0 && gy < jd->h) {
                 if (src == 1) {
-                    const int o = D[gcell(r, c)];
-                    v = o < GD_INF ? o : GD_INF;
-                } else if (M[gmask(r, c)] && __ldg(sd + (int64_t)gy * jd->pb + gx)) {
-                    v = 0;
+                    const int4 o4 = *dp;
+                    const int o[4] = {o4.x, o4.y, o4.z, o4.w};
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int c = c0 + b, gx = x0 - 1 + c;
+                        if (c >= 0 && c < RR && gx >= 0 && gx < jd->w) v[b] = min(o[b], GD_INF);
+                    }
+                } else {
+                    const unsigned mw = *(const unsigned *)(M + r * BU8_W + 4 * q + 12);
+                    uint8_t sv[4] = {0, 0, 0, 0};
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int c = c0 + b, gx = x0 - 1 + c;
+                        if (c >= 0 && c < RR && gx >= 0 && gx < jd->w && ((mw >> (8 * b)) & 0xFFu))
+                            sv[b] = __ldg(sd + (int64_t)gy * jd->pb + gx);
+                    }
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        if (sv[b]) v[b] = 0;
                 }
             }
-            D[gcell(r, c)] = v;
+            *dp = make_int4(v[0], v[1], v[2], v[3]);
         }
     }
     __syncthreads();
