@@ -93,7 +93,7 @@ static_assert(
 // second queue buffer) must not overlap the binary box or the first buffer
 static_assert(BU8_BYTES <= 2 * QCAP_E * 2 - 320 && QCAP_E * 2 <= 2 * QCAP_E * 2 - 320, "EDT change flags");
 // the wide-window pass's box (tile + 8-pixel halo, int32) fits the layout
-static_assert(E_W + (TS + 16) * (TS + 16) * 4 <= E_BYTES, "EDT wide-window box");
+static_assert(E_W + (TS + 16) * (TS + 16) * 4 + 32 <= E_BYTES, "EDT wide-window box and its change masks");
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 // geodesic distance: D as the int32 box layout (stride 72, cell (r, c) at
@@ -1659,11 +1659,20 @@ __device__ bool edt_wide_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
     //    only by its own thread; a window cell read while its owner updates
     //    it gives the old or the new feature, both valid candidates, and a
     //    pass that changes nothing has compared every pixel with every
-    //    window cell at its final value.
+    //    window cell at its final value.  After the first pass, a pixel
+    //    whose window held no pixel the previous pass changed saw all its
+    //    window cells at their present values then, so it cannot change
+    //    and is skipped; the rows and columns the pass changed pixels in
+    //    (64-bit masks CH[0] / CH[1]; CH[2] / CH[3] for the pass running)
+    //    bound the windows that did.
+    unsigned long long *CH = (unsigned long long *)(sm + E_W + B * B * 4);
+    if (tid < 4) CH[tid] = 0;
+    __syncthreads();
     bool any = false;
     int sets = 0;
     while (true) {
         bool ch = false;
+        const unsigned long long prow = CH[0], pcol = CH[1];
         for (int k = tid; k < TS * TS; k += NT) {
             const int ri = k / TS, ci = k - ri * TS;
             if (y0 + ri >= jd->h || x0 + ci >= jd->w) continue;
@@ -1677,6 +1686,13 @@ __device__ bool edt_wide_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
 #pragma unroll
             for (int j = 0; j < K - 1; ++j) kw += u >= (unsigned)ka.wide_u[j] ? 1 : 0;
             if (kw == 1 && first && sets == 0 && ri > 0 && ri < TS - 1 && ci > 0 && ci < TS - 1) continue;
+            if (sets > 0) {
+                const int r0 = max(0, ri - kw), r1 = min(TS - 1, ri + kw);
+                const int c0 = max(0, ci - kw), c1 = min(TS - 1, ci + kw);
+                const unsigned long long mr = (~0ull >> (63 - (r1 - r0))) << r0;
+                const unsigned long long mc = (~0ull >> (63 - (c1 - c0))) << c0;
+                if (!(prow & mr) || !(pcol & mc)) continue;
+            }
             unsigned last = VR_INF;
             for (int dy = -kw; dy <= kw; ++dy) {
                 const unsigned *row = V + i + dy * B;
@@ -1691,12 +1707,21 @@ __device__ bool edt_wide_visit(const KArgs &ka, const JobDesc *jd, int gt, char 
             if (b != f) {
                 V[i] = b;
                 ch = true;
+                atomicOr(CH + 2, 1ull << ri);
+                atomicOr(CH + 3, 1ull << ci);
                 wide_flag(hdr, jd, tx, ty, ri, ci, K);
             }
         }
         ++sets;
         if (!__syncthreads_or(ch)) break;
         any = true;
+        if (tid == 0) {  // this pass's masks become the previous pass's
+            CH[0] = CH[2];
+            CH[1] = CH[3];
+            CH[2] = 0;
+            CH[3] = 0;
+        }
+        __syncthreads();
         // a guard only (every pass that changes something improves a pixel,
         // so the loop ends); thread 0 decides for the whole block
         if (__syncthreads_or(tid == 0 && globaltimer_ns() > deadline)) {
