@@ -207,8 +207,11 @@ __global__ void __launch_bounds__(ET) rows_envelope_kernel(ExactArgs a, int C) {
     uint16_t *own = (uint16_t *)(S + (size_t)ET * (C + 1));
     int *lo = (int *)(own + (size_t)ET * (C + 2));
     int *hi = lo + ET;
-    int *prv = hi + ET;    // the last non-empty chunk at or before c (-1: none)
-    int *nxt = prv + ET;   // the first non-empty chunk at or after c (ET: none)
+    // during the merges: each group's first / last non-empty chunk (indexed
+    // by the group's first chunk); from step 3: the last non-empty chunk at
+    // or before c (-1: none) / the first at or after c (ET: none)
+    int *prv = hi + ET;
+    int *nxt = prv + ET;
     int *wsum = nxt + ET;  // per-warp partial results of the scans
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, w = a.w;
     const int CO = C + 2, CP = C >> 5;  // CP: 32-column parts per chunk (1 or 2)
