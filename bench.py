@@ -315,7 +315,36 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def bench_batched(ctx, dev, n, reps):
+def oracle_all_cores(items):
+    """The oracle over independent images, one image per host core at a
+    time (a thread pool: the C oracle releases the GIL while it runs).
+    items: (op, arrays) with op "recon" (marker, mask) or "edt" (binary).
+    Returns (seconds, threads used)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import numpy as np
+
+    import oracle
+
+    cores = len(os.sched_getaffinity(0)) or os.cpu_count() or 1
+    z = np.zeros((2, 2), np.uint8)
+    oracle.fh(z, z, 8)  # builds and loads the C oracle before the threads start
+    oracle.edt(z)
+
+    def run(item):
+        op, arrs = item
+        if op == "recon":
+            oracle.fh(arrs[0], arrs[1], 8)
+        else:
+            oracle.edt(arrs[0])
+
+    t = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(run, items))
+    return time.perf_counter() - t, cores
+
+
+def bench_batched(ctx, dev, n, reps, cpu=False):
     """512 mixed images (sides log-uniform 256..2048, half reconstruction,
     half EDT) in ONE persistent launch from an autotuned plan replayed as a
     CUDA graph, against one launch per image on the same GPU."""
@@ -367,7 +396,14 @@ def bench_batched(ctx, dev, n, reps):
     ctx.sync()
     base_ms = a.elapsed_time(b)
     plan.close()
+    cpu_res = None
+    if cpu:
+        sec, cores = oracle_all_cores([("recon", (wl.marker, wl.mask)) if wl.op == "recon" else ("edt", (wl.binary,))
+                                       for wl in wls])
+        cpu_res = {"imgs_s": round(n / sec, 1), "mpx_s": round(px / sec / 1e6, 1), "cores": cores, "kind": "oracle",
+                   "sample": f"the whole {n}-image batch, one image per core at a time"}
     return {"images": n, "pixels": px, "ms_per_batch": round(ms, 3), "imgs_s": round(n / ms * 1e3, 1),
+            "cpu_oracle": cpu_res,
             "mpx_s": round(px / ms / 1e3, 1), "one_per_launch_ms": round(base_ms, 3),
             "one_per_launch_imgs_s": round(n / base_ms * 1e3, 1), "speedup": round(base_ms / ms, 2),
             "launch": ("one persistent launch per operation family (uint8 reconstruction, distance transform), "
@@ -378,7 +414,7 @@ def bench_batched(ctx, dev, n, reps):
             "tile": "64x64 (fixed)"}
 
 
-def bench_served(ctx, dev, rates, duration, budget, min_requests=2000):
+def bench_served(ctx, dev, rates, duration, budget, min_requests=2000, cpu=False):
     """Poisson arrivals of mixed reconstruction / EDT requests, square sides
     log-uniform 512..8192 (host images, pinned), served by the
     continuous-batching server under an HBM budget, against one job per
@@ -471,8 +507,20 @@ def bench_served(ctx, dev, rates, duration, budget, min_requests=2000):
             "one_per_launch": {"req_s": round(len(seq) / base_span, 1), "mpx_s": round(px / base_span / 1e6, 1),
                                "p50_ms": round(float(np.percentile(base_lat, 50)), 3),
                                "p99_ms": round(float(np.percentile(base_lat, 99)), 3)}}
+    cpu_res = None
+    if cpu:
+        # the request mix (each template twice) through the oracle, one
+        # request per host core at a time: the rate the host alone sustains
+        items = [("recon", (t["marker"].numpy(), t["mask"].numpy())) if t["op"] == "recon" else
+                 ("edt", (t["binary"].numpy(),)) for t in templates * 2]
+        sec, cores = oracle_all_cores(items)
+        mpx = 2 * sum(t["px"] for t in templates) / 1e6
+        cpu_res = {"req_s": round(len(items) / sec, 2), "mpx_s": round(mpx / sec, 1), "cores": cores,
+                   "kind": "oracle", "sample": f"the {len(templates)} request templates, twice each, one request "
+                                               f"per core at a time"}
     return {"duration_s": duration, "hbm_budget_gb": round(budget / 2**30, 1),
-            "sizes": "square sides log-uniform 512..8192, alternating recon / EDT", "rates": results}
+            "sizes": "square sides log-uniform 512..8192, alternating recon / EDT", "rates": results,
+            "cpu_oracle": cpu_res}
 
 
 def bench_queue_ablation(ctx, dev, reps=5):
@@ -978,7 +1026,7 @@ def run_gpu(args, ws, rank, local):
 
     batched = served = None
     if rank == 0 and not args.skip_batched:
-        batched = bench_batched(ctx, dev, args.batch_images, max(1, args.steps // 2))
+        batched = bench_batched(ctx, dev, args.batch_images, max(1, args.steps // 2), cpu=not args.no_cpu_baseline)
     coverage = None
     if rank == 0 and not args.skip_coverage:
         coverage = bench_coverage(ctx, dev, d_marker, d_mask, side)
@@ -999,7 +1047,7 @@ def run_gpu(args, ws, rank, local):
         ablation = bench_queue_ablation(ctx, dev)
     if rank == 0 and not args.skip_served:
         rates = [int(r) for r in args.serve_rates.split(",") if r]
-        served = bench_served(ctx, dev, rates, args.serve_duration, 120 << 30)
+        served = bench_served(ctx, dev, rates, args.serve_duration, 120 << 30, cpu=not args.no_cpu_baseline)
 
     traffic = profiled_traffic(f"persistent_{dominant}", side)
     visits = None
