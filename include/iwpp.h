@@ -402,6 +402,8 @@ int iwpp_plan_destroy(iwpp_plan *plan);
  * (each with its own resident context), and keeps admitting new arrivals
  * onto free streams while earlier batches run.  Results are copied back to
  * the request's host buffers; the latency reported is submit-to-completion.
+ * The request images come from a memory pool of the server's own, which
+ * never makes one stream wait for another's frees.
  * Admission counts, against the budget, the images of every request in
  * flight and the device memory of every stream's context (its workspace
  * grows to the largest batch it has run and stays resident).  A request
@@ -429,8 +431,8 @@ typedef struct {
     uint64_t bytes_in_use;       /* request images in flight + resident workspaces */
     uint64_t peak_bytes_in_use;  /* peak of bytes_in_use (admission keeps it <= budget) */
     uint64_t workspace_bytes;    /* device memory the streams' contexts hold */
-    uint64_t pool_used_high;     /* high-water mark of the device's default memory
-                                    pool (request images) since server creation */
+    uint64_t pool_used_high;     /* high-water mark of the server's memory pool
+                                    (request images) since server creation */
     uint64_t records;            /* finished results not yet handed out */
 } iwpp_server_stats_t;
 

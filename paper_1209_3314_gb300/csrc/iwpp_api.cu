@@ -11,6 +11,7 @@
 
 #include "../../include/iwpp.h"
 #include "iwpp_internal.h"
+#include "iwpp_status.h"
 
 using namespace iwpp;
 
@@ -1213,24 +1214,12 @@ int ctx_device_bytes_after(iwpp_ctx *ctx, int n, const int *op, const int *dtype
     return IWPP_OK;
 }
 
-}  // namespace iwpp
-
-extern "C" {
-
-int iwpp_sync(iwpp_ctx *ctx, void *stream) {
-    if (!ctx) return IWPP_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
-    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+int status_readback(iwpp_ctx *ctx, cudaStream_t st) {
     CK(cudaMemcpyAsync(ctx->h_ctl, ctx->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st), "status readback");
-    CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
-    for (auto &ev : ctx->pending_events) {
-        float ms = 0.f;
-        CK(cudaEventSynchronize(ev.second), "cudaEventSynchronize");
-        CK(cudaEventElapsedTime(&ms, ev.first, ev.second), "cudaEventElapsedTime");
-        ctx->kernel_ns += (uint64_t)((double)ms * 1e6);
-        ctx->free_events.push_back(ev);
-    }
-    ctx->pending_events.clear();
+    return IWPP_OK;
+}
+
+int status_result(iwpp_ctx *ctx, cudaStream_t st) {
     const int errors = ctx->h_ctl->errors;
     if (errors) {
         CK(cudaMemsetAsync(&ctx->ctl->errors, 0, sizeof(int), st), "status reset");
@@ -1241,6 +1230,28 @@ int iwpp_sync(iwpp_ctx *ctx, void *stream) {
         return fail(ctx, IWPP_EOVERFLOW, "tile queue overflowed after %d relaunches; raise queue_factor or max_relaunch",
                     ctx->opt.max_relaunch);
     return IWPP_OK;
+}
+
+}  // namespace iwpp
+
+extern "C" {
+
+int iwpp_sync(iwpp_ctx *ctx, void *stream) {
+    if (!ctx) return IWPP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int rc = iwpp::status_readback(ctx, st);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    for (auto &ev : ctx->pending_events) {
+        float ms = 0.f;
+        CK(cudaEventSynchronize(ev.second), "cudaEventSynchronize");
+        CK(cudaEventElapsedTime(&ms, ev.first, ev.second), "cudaEventElapsedTime");
+        ctx->kernel_ns += (uint64_t)((double)ms * 1e6);
+        ctx->free_events.push_back(ev);
+    }
+    ctx->pending_events.clear();
+    return iwpp::status_result(ctx, st);
 }
 
 int iwpp_stats(iwpp_ctx *ctx, iwpp_stats_t *out) {

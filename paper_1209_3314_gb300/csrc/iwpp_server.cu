@@ -5,17 +5,23 @@
 //   * admission: a request is admitted when the device memory it needs
 //     fits the server's HBM budget next to everything else the server holds:
 //     the images of the requests in flight (stream-ordered allocations from
-//     the device's memory pool, which keeps freed blocks cached for the next
-//     requests) and the resident workspace of every stream's context, grown
-//     to what the batch needs (tile queue, tile states, spill queues);
+//     the server's own memory pool, which keeps freed blocks cached for the
+//     next requests) and the resident workspace of every stream's context,
+//     grown to what the batch needs (tile queue, tile states, spill queues);
+//   * the pool never makes one stream wait for another to reuse a block
+//     (no internal dependencies): a stream reuses its own freed blocks, or
+//     blocks whose free has completed, and otherwise takes new memory, so
+//     the streams' batches overlap instead of queueing behind each other's
+//     frees;
 //   * batching: the admitted requests form one batch, run as ONE persistent
 //     launch (iwpp_run_jobs_async) on one of the server's streams; each
 //     stream has its own resident context (tile queue, flags, spill space);
 //   * continuous: while batches run on some streams, newly arrived requests
 //     are admitted and launched on the others as soon as memory and a
 //     stream are free, so their work overlaps on the device;
-//   * completion: host-to-device copies, the launch and device-to-host
-//     copies are ordered on the batch's stream; an event marks the end.
+//   * completion: host-to-device copies, the launch, device-to-host copies
+//     and the readback of the batch's status are ordered on the batch's
+//     stream; an event marks the end.
 //     The worker polls the events, releases the memory, and records each
 //     request's status and latency (submit to completion), which
 //     iwpp_server_poll / iwpp_server_wait hand out once (then the ticket is
@@ -33,6 +39,7 @@
 
 #include "../../include/iwpp.h"
 #include "iwpp_internal.h"
+#include "iwpp_status.h"
 
 namespace {
 
@@ -113,7 +120,7 @@ bool iwpp_server::launch(Slot &s, std::vector<Request> &&batch) {
         j.flags = r.flags;
         auto dev_alloc = [&](size_t n) -> void * {
             void *p = nullptr;
-            if (cudaMallocAsync(&p, std::max<size_t>(n, 1), st) != cudaSuccess) {
+            if (cudaMallocFromPoolAsync(&p, std::max<size_t>(n, 1), pool, st) != cudaSuccess) {
                 ok = false;
                 return nullptr;
             }
@@ -149,6 +156,10 @@ bool iwpp_server::launch(Slot &s, std::vector<Request> &&batch) {
             ok = cudaMemcpyAsync(r.sqdist, jobs[i].sqdist, 4 * px, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
                  cudaMemcpyAsync(r.nearest, jobs[i].nearest, 4 * px, cudaMemcpyDeviceToHost, st) == cudaSuccess;
     }
+    // the batch's status follows its own copies on its stream, so reading
+    // it needs no later copy (which would queue behind other streams'
+    // transfers and hold up this thread)
+    if (ok) ok = iwpp::status_readback(s.ctx, st) == IWPP_OK;
     for (void *p : s.allocs) cudaFreeAsync(p, st);  // stream-ordered: after the copies
     s.allocs.clear();
     if (ok) ok = cudaEventRecord(s.done, st) == cudaSuccess;
@@ -158,8 +169,8 @@ bool iwpp_server::launch(Slot &s, std::vector<Request> &&batch) {
 }
 
 void iwpp_server::finish(Slot &s) {
-    // the stream is idle: read the batch's device status
-    const int rc = iwpp_sync(s.ctx, s.stream);
+    // the stream is idle: the batch's status has arrived
+    const int rc = iwpp::status_result(s.ctx, s.stream);
     const Clock::time_point t1 = Clock::now();
     std::lock_guard<std::mutex> lock(mu);
     for (Request &r : s.batch) {
@@ -271,12 +282,25 @@ int iwpp_server_create(iwpp_server **out, int device, size_t hbm_budget_bytes, i
     s->budget = hbm_budget_bytes;
     s->max_batch = max_batch;
     s->slots.resize(streams);
-    // keep freed pool memory cached up to the budget: admission, not the
-    // allocator, bounds the footprint
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
-        uint64_t thr = hbm_budget_bytes;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    // the server's pool: freed memory stays cached up to the budget
+    // (admission, not the allocator, bounds the footprint), and no reuse
+    // across streams through inserted dependencies
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
+        s->pool = nullptr;
+        iwpp_server_destroy(s);
+        return IWPP_ECUDA;
+    }
+    uint64_t thr = hbm_budget_bytes;
+    int no = 0;
+    if (cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &thr) != cudaSuccess ||
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowInternalDependencies, &no) != cudaSuccess) {
+        iwpp_server_destroy(s);
+        return IWPP_ECUDA;
     }
     for (Slot &sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -291,13 +315,6 @@ int iwpp_server_create(iwpp_server **out, int device, size_t hbm_budget_bytes, i
     if (s->ws_total > hbm_budget_bytes) {
         iwpp_server_destroy(s);
         return IWPP_ENOMEM;
-    }
-    // the pool's high-water mark of memory in use starts from now
-    if (cudaDeviceGetDefaultMemPool(&s->pool, device) == cudaSuccess) {
-        uint64_t zero = 0;
-        cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrUsedMemHigh, &zero);
-    } else {
-        s->pool = nullptr;
     }
     s->worker = std::thread([s] { s->run(); });
     *out = s;
@@ -388,6 +405,7 @@ int iwpp_server_destroy(iwpp_server *s) {
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     delete s;
     return IWPP_OK;
 }
